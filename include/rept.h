@@ -1,0 +1,189 @@
+/*
+ * rept.h -- C ABI of the GB300 REPT streaming semi-triangle counter.
+ *
+ * REPT (Wang et al., "REPT: A Streaming Algorithm of Approximating Global
+ * and Local Triangle Counts in Parallel") splits an edge stream among c
+ * processors with a hash h: each processor i keeps the edges of one colour
+ * and, for every arriving edge (u, v), counts the common neighbours of u and
+ * v among the edges it already keeps (Algorithm 1, UpdateTriangleCNT).  The
+ * counts tau^(i), tau_v^(i) are combined into estimates of the global and
+ * local triangle counts (Section III-A for c <= m, Section III-B.1 for c > m
+ * with c mod m = 0).
+ *
+ * Conventions shared by every entry point
+ *   - Processors are 0-based: processor i = k*m + j (i < c) is slot j of hash
+ *     group k and keeps the edges e with h_k(e) = j, where
+ *       h_k(u, v) = SplitMix64(((min(u,v) << 32) | max(u,v)) ^ s_k) mod m,
+ *       s_k       = seed + k * 0x9E3779B97F4A7C15 (mod 2^64),
+ *     SplitMix64(x) being one output step of that generator from state x
+ *     (the state is advanced by 0x9E3779B97F4A7C15 before mixing).
+ *   - Stream indices are 0-based and global to a handle: the first edge of a
+ *     batch follows the last edge of the previous batch.  Batch boundaries
+ *     never change any count (the result equals the sequential algorithm).
+ *   - Node ids lie in [0, n_nodes).  A self-loop (u == v) is skipped: not
+ *     stored, not counted, and tallied in rept_stats.self_loops.  A stream
+ *     must not repeat an undirected edge (the paper's E is a set); repeated
+ *     edges give undefined counts.
+ *   - `stream` arguments are cudaStream_t values passed as void*; NULL means
+ *     the legacy default stream.  All device work of a call is enqueued on
+ *     that stream in order.
+ *   - Device pointers ("d_" prefix) must point to memory of the device that
+ *     was current when the handle was created; host pointers ("h_") to
+ *     ordinary or pinned host memory.
+ *   - Return value: REPT_OK (0) or a negative REPT_E_* code.  Errors detected
+ *     on the device (an id >= n_nodes, an exhausted fixed pool, an internal
+ *     probe bound) make the handle's status sticky: the failing batch and
+ *     every later batch are not applied (the counts stay those of the last
+ *     good batch), and the error is returned by the next call that
+ *     synchronises (rept_estimates*, rept_counts, rept_stats, rept_sync, or
+ *     any ingest when REPT_FLAG_SYNC is set).  rept_reset clears it.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef REPT_H
+#define REPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define REPT_OK 0
+#define REPT_E_INVAL (-1)     /* bad argument (m, c or n_nodes zero, NULL pointer, unsupported c) */
+#define REPT_E_RANGE (-2)     /* an edge endpoint >= n_nodes (device-detected, batch not applied) */
+#define REPT_E_CAPACITY (-3)  /* REPT_FLAG_FIXED_POOL set and the adjacency pool is full (batch not applied) */
+#define REPT_E_NOMEM (-4)     /* a device or pinned-host allocation failed */
+#define REPT_E_CUDA (-5)      /* a CUDA runtime call failed */
+#define REPT_E_TIMEOUT (-6)   /* a bounded device-side wait gave up (batched persistent path) */
+#define REPT_E_INTERNAL (-7)  /* a device-side invariant failed (bounded probe found no slot) */
+
+#define REPT_FLAG_FIXED_POOL 1u /* never grow the adjacency pool; a full pool gives REPT_E_CAPACITY */
+#define REPT_FLAG_SYNC 2u       /* synchronise at the end of every ingest and report errors at once */
+#define REPT_FLAG_PROFILE 4u    /* time every kernel launch with CUDA events on its stream (rept_kernel_times) */
+#define REPT_FLAG_WORK_COUNTERS 8u /* count the intersection's table reads into rept_stats (slower; not for timing) */
+
+/* kernel ids used by rept_kernel_times */
+#define REPT_K_CLASSIFY 0
+#define REPT_K_PLAN 1
+#define REPT_K_COMMIT 2
+#define REPT_K_INSERT 3
+#define REPT_K_INTERSECT 4
+#define REPT_K_ESTIMATE 5
+#define REPT_NUM_KERNELS 6
+
+typedef struct rept_config {
+    uint32_t m;              /* 1/p; m >= 1 (the paper takes m >= 2; m = 1 keeps every edge) */
+    uint32_t c;              /* number of processors, c >= 1; c > m requires c % m == 0 */
+    uint64_t seed;           /* hash seed s_0 */
+    uint32_t n_nodes;        /* node ids are < n_nodes; 1 <= n_nodes < 2^32 - 1 */
+    uint32_t flags;          /* REPT_FLAG_* */
+    uint64_t expected_edges; /* sizing hint: edges the stream will carry (0: start small and grow) */
+    uint64_t max_batch;      /* sizing hint: largest batch passed to an ingest call (0: 2^20) */
+} rept_config;
+
+typedef struct rept_stats {
+    uint64_t edges;          /* edges ingested (including self-loops) */
+    uint64_t self_loops;     /* self-loops skipped */
+    uint64_t stored_edges;   /* edges kept by at least one processor (union adjacency) */
+    uint64_t pool_slots;     /* adjacency pool capacity in 8-byte slots */
+    uint64_t pool_used;      /* slots handed out to per-node tables so far */
+    uint64_t device_bytes;   /* device memory held by the handle */
+    /* with REPT_FLAG_WORK_COUNTERS, totals over the stream's intersection passes: */
+    uint64_t small_entries;  /* entries present in the smaller endpoint's table, summed over edges */
+    uint64_t small_slots;    /* slots of those tables read (entries plus empty slots) */
+    uint64_t probes;         /* probes of the larger endpoint's table (small-side entries older than the edge) */
+    uint64_t probe_slots;    /* slots read by those probes */
+    uint64_t wedges;         /* closed wedges found in the union adjacency (both edges older than the edge) */
+    uint64_t counted;        /* (wedge, hash group) pairs counted for some processor */
+} rept_stats;
+
+typedef struct rept_state rept_state;
+
+/*
+ * rept_create: allocate an empty stream state (all tau^(i), tau_v^(i) = 0,
+ * every E^(i) empty; Algorithm 1's initialisation) on the current device.
+ * `cfg` is copied; `*out` receives the handle (owned by the caller, released
+ * with rept_destroy).  Returns REPT_E_INVAL for m == 0, c == 0, n_nodes == 0
+ * or c > m with c % m != 0; REPT_E_NOMEM / REPT_E_CUDA on allocation failure.
+ */
+int rept_create(const rept_config* cfg, void* stream, rept_state** out);
+
+/* rept_reset: return the handle to the empty stream, keeping its allocations; clears a sticky error. */
+int rept_reset(rept_state* s, void* stream);
+
+/*
+ * rept_ingest_batch: append n edges (d_src[t], d_dst[t]), t < n, to the
+ * stream and process them exactly as Algorithm 1 would, one edge after the
+ * other: every edge first closes the wedges of edges that arrived before it
+ * and are kept by a common processor (counted for every processor whose
+ * colour both wedge edges carry), then is stored by the processors that keep
+ * it.  d_src / d_dst are device arrays of n uint32 node ids, caller-owned,
+ * and must stay valid and unchanged until the stream reaches this work.
+ * Asynchronous on `stream`, except that the call may synchronise once to
+ * grow the adjacency pool (never with REPT_FLAG_FIXED_POOL).  n == 0 is a
+ * no-op.  Errors: REPT_E_INVAL (NULL pointers with n > 0), REPT_E_NOMEM,
+ * REPT_E_CUDA; device-detected errors as described above.
+ */
+int rept_ingest_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n, void* stream);
+
+/*
+ * rept_ingest_host: the same for host arrays h_src / h_dst of n edges.  The
+ * edges are copied to device staging buffers owned by the handle in chunks
+ * of at most `batch` edges (0: the handle's max_batch) and each chunk is
+ * ingested as one batch.  Returns after the last chunk has been enqueued and
+ * its host buffers may be reused (the call synchronises on the copies).
+ */
+int rept_ingest_host(rept_state* s, const uint32_t* h_src, const uint32_t* h_dst, uint64_t n, uint64_t batch,
+                     void* stream);
+
+/*
+ * rept_estimates: FP64 estimates from the counts so far.
+ *   c <= m              : tau_hat = (m^2 / c) * sum_i tau^(i),  tau_hat_v likewise   (Section III-A)
+ *   c > m, c % m == 0   : tau_hat = (m / c1) * sum_i tau^(i), c1 = c / m              (Section III-B.1)
+ * Each scale factor is formed in double and multiplied by the exactly
+ * converted integer sum.  h_global: host double (required).  d_local: device
+ * array of n_nodes doubles, or NULL to skip the local estimates.
+ * Synchronises `stream`; returns any sticky device error.
+ */
+int rept_estimates(rept_state* s, double* h_global, double* d_local, void* stream);
+
+/* rept_estimates_host: as rept_estimates, with the local estimates written to host memory h_local (or NULL). */
+int rept_estimates_host(rept_state* s, double* h_global, double* h_local, void* stream);
+
+/*
+ * rept_counts: the integer counters.  h_proc: host array of c uint64
+ * (tau^(i), processor i = k*m + j), or NULL.  d_local: device array of
+ * n_nodes uint64 receiving sum_i tau_v^(i) over all processors, or NULL.
+ * Synchronises `stream`; returns any sticky device error.
+ */
+int rept_counts(rept_state* s, uint64_t* h_proc, uint64_t* d_local, void* stream);
+
+/* rept_stats: counters describing the handle (see rept_stats).  Synchronises `stream`. */
+int rept_get_stats(rept_state* s, rept_stats* out, void* stream);
+
+/*
+ * rept_kernel_times: with REPT_FLAG_PROFILE, the summed CUDA-event durations
+ * (milliseconds) and launch counts of each kernel (REPT_K_* order) since
+ * create or the previous call with `clear` != 0 (rept_reset keeps them).  ms and launches are
+ * host arrays of REPT_NUM_KERNELS entries (either may be NULL).  Synchronises
+ * the handle's recorded events.  REPT_E_INVAL without REPT_FLAG_PROFILE.
+ */
+int rept_kernel_times(rept_state* s, double* ms, uint64_t* launches, int clear);
+
+/* rept_sync: wait for `stream` and return the handle's sticky device error, if any. */
+int rept_sync(rept_state* s, void* stream);
+
+/* rept_destroy: free every allocation of the handle (NULL is a no-op).  Waits for the handle's pending work. */
+void rept_destroy(rept_state* s);
+
+/* rept_strerror: static English text for a REPT_* code. */
+const char* rept_strerror(int code);
+
+/* rept_kernel_launches: kernels this library has launched in this process (all handles). */
+uint64_t rept_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REPT_H */

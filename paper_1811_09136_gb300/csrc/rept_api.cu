@@ -1,0 +1,492 @@
+// C ABI of the REPT streaming counter (declared in include/rept.h): handle
+// lifetime, pool sizing, batch launch sequence, estimates.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "rept.h"
+#include "rept_common.cuh"
+#include "rept_kernels.cuh"
+
+using namespace rept;
+
+namespace {
+
+std::atomic<unsigned long long> g_launches{0};
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+#define REPT_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t _e = (call);                          \
+        if (_e != cudaSuccess) {                          \
+            if (_e == cudaErrorMemoryAllocation) {        \
+                (void)cudaGetLastError();                 \
+                return REPT_E_NOMEM;                      \
+            }                                             \
+            return REPT_E_CUDA;                           \
+        }                                                 \
+    } while (0)
+
+#define REPT_LAUNCHED()                                   \
+    do {                                                  \
+        g_launches.fetch_add(1, std::memory_order_relaxed); \
+        if (cudaPeekAtLastError() != cudaSuccess) {       \
+            (void)cudaGetLastError();                     \
+            return REPT_E_CUDA;                           \
+        }                                                 \
+    } while (0)
+
+int status_to_code(unsigned st) {
+    if (st & kStRange) return REPT_E_RANGE;
+    if (st & kStCapacity) return REPT_E_CAPACITY;
+    if (st & kStTimeout) return REPT_E_TIMEOUT;
+    if (st & kStInternal) return REPT_E_INTERNAL;
+    return REPT_OK;
+}
+
+}  // namespace
+
+struct rept_state {
+    rept_config cfg{};
+    int device = 0;
+    int sm_count = 0;
+    uint32_t groups = 1;
+    StreamDev d{};
+    unsigned long long max_batch = 0;
+    unsigned long long next_t = 0;  // stream index of the next edge
+    Ctrl* h_ctrl = nullptr;         // pinned mirror of the control block
+    uint32_t* stage_src = nullptr;  // device staging for rept_ingest_host
+    uint32_t* stage_dst = nullptr;
+    unsigned long long stage_cap = 0;
+    double* d_global = nullptr;
+    double* h_global = nullptr;  // pinned
+    double* d_local_tmp = nullptr;
+    int grid_stream = 0;     // blocks for edge/node-parallel kernels
+    int grid_intersect = 0;  // blocks for k_intersect
+    size_t device_bytes = 0;
+    // REPT_FLAG_PROFILE: event pairs recorded around launches, folded into totals on query
+    struct Timed { int kernel; cudaEvent_t start, stop; };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> spare_events;
+    double kernel_ms[REPT_NUM_KERNELS] = {0};
+    unsigned long long kernel_launches[REPT_NUM_KERNELS] = {0};
+};
+
+namespace {
+
+int dev_alloc(rept_state* s, void** p, size_t bytes) {
+    REPT_CUDA(cudaMalloc(p, bytes));
+    s->device_bytes += bytes;
+    return REPT_OK;
+}
+
+void dev_free(rept_state* s, void* p, size_t bytes) {
+    if (p) {
+        cudaFree(p);
+        s->device_bytes -= bytes;
+    }
+}
+
+// Pool slots that guarantee no batch can run out: every node's allocations form a
+// doubling series bounded by twice its final capacity, itself at most 4 * cnt, so
+// at most 8 slots per stored entry, i.e. 16 slots (4 quads) per stream edge.
+unsigned long long quads_bound(unsigned long long edges) { return 4ull * edges + 64ull; }
+
+int grow_pool(rept_state* s, unsigned long long min_quads, cudaStream_t st) {
+    unsigned long long want = std::max(min_quads, 2ull * s->d.pool_quads);
+    if (want > 0xFFFFFFFFull) want = 0xFFFFFFFFull;  // offsets are 32-bit quads
+    if (want < min_quads) return REPT_E_CAPACITY;
+    uint2* np = nullptr;
+    int rc = dev_alloc(s, (void**)&np, want * 32ull);
+    if (rc) return rc;
+    REPT_CUDA(cudaStreamSynchronize(st));
+    const unsigned long long used = s->h_ctrl->pool_top;
+    if (s->d.pool && used) REPT_CUDA(cudaMemcpyAsync(np, s->d.pool, used * 32ull, cudaMemcpyDeviceToDevice, st));
+    REPT_CUDA(cudaMemsetAsync((char*)np + used * 32ull, 0xFF, (want - used) * 32ull, st));
+    REPT_CUDA(cudaStreamSynchronize(st));
+    dev_free(s, s->d.pool, s->d.pool_quads * 32ull);
+    s->d.pool = np;
+    s->d.pool_quads = want;
+    return REPT_OK;
+}
+
+int read_ctrl(rept_state* s, cudaStream_t st) {
+    REPT_CUDA(cudaMemcpyAsync(s->h_ctrl, s->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    REPT_CUDA(cudaStreamSynchronize(st));
+    return REPT_OK;
+}
+
+int ensure_batch_scratch(rept_state* s, unsigned long long n, cudaStream_t st) {
+    if (n <= s->max_batch) return REPT_OK;
+    REPT_CUDA(cudaStreamSynchronize(st));
+    const unsigned long long old = s->max_batch;
+    dev_free(s, s->d.touched, 2 * old * sizeof(uint32_t));
+    dev_free(s, s->d.grow_rel, 2 * old * sizeof(uint32_t));
+    s->d.touched = nullptr;
+    s->d.grow_rel = nullptr;
+    int rc = dev_alloc(s, (void**)&s->d.touched, 2 * n * sizeof(uint32_t));
+    if (!rc) rc = dev_alloc(s, (void**)&s->d.grow_rel, 2 * n * sizeof(uint32_t));
+    if (rc) return rc;
+    s->max_batch = n;
+    return REPT_OK;
+}
+
+cudaEvent_t take_event(rept_state* s) {
+    if (!s->spare_events.empty()) {
+        cudaEvent_t e = s->spare_events.back();
+        s->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Launch `fn` on `st`; with REPT_FLAG_PROFILE bracket it with events on the same stream.
+template <class F>
+int timed_launch(rept_state* s, int kernel, cudaStream_t st, F&& fn) {
+    const bool prof = (s->cfg.flags & REPT_FLAG_PROFILE) != 0;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (prof) {
+        a = take_event(s);
+        b = take_event(s);
+        if (!a || !b) return REPT_E_CUDA;
+        REPT_CUDA(cudaEventRecord(a, st));
+    }
+    fn();
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    s->kernel_launches[kernel] += 1;
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        (void)cudaGetLastError();
+        return REPT_E_CUDA;
+    }
+    if (prof) {
+        REPT_CUDA(cudaEventRecord(b, st));
+        s->timed.push_back({kernel, a, b});
+    }
+    return REPT_OK;
+}
+
+int fold_times(rept_state* s) {
+    for (auto& t : s->timed) {
+        REPT_CUDA(cudaEventSynchronize(t.stop));
+        float ms = 0.f;
+        REPT_CUDA(cudaEventElapsedTime(&ms, t.start, t.stop));
+        s->kernel_ms[t.kernel] += ms;
+        s->spare_events.push_back(t.start);
+        s->spare_events.push_back(t.stop);
+    }
+    s->timed.clear();
+    return REPT_OK;
+}
+
+int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, unsigned long long n, cudaStream_t st) {
+    BatchDev b{d_src, d_dst, n, s->next_t};
+    const int threads = 256;
+    const unsigned long long want_blocks = (n + threads - 1) / threads;
+    const int grid = (int)std::min<unsigned long long>(want_blocks, (unsigned long long)s->grid_stream);
+    int rc = REPT_OK;
+    if ((rc = timed_launch(s, REPT_K_CLASSIFY, st, [&] { k_classify<<<grid, threads, 0, st>>>(s->d, b); })))
+        return rc;
+    if ((rc = timed_launch(s, REPT_K_PLAN, st, [&] { k_plan<<<grid, threads, 0, st>>>(s->d); }))) return rc;
+    const bool fixed = (s->cfg.flags & REPT_FLAG_FIXED_POOL) != 0;
+    if (!fixed && s->d.pool_quads < quads_bound(s->next_t + n)) {
+        // not provably large enough: read this batch's request and grow if needed
+        if ((rc = read_ctrl(s, st))) return rc;
+        const unsigned long long need = s->h_ctrl->pool_top + s->h_ctrl->need_quads;
+        if (s->h_ctrl->status == 0u && need > s->d.pool_quads) {
+            if ((rc = grow_pool(s, need + need / 2 + 1024, st))) return rc;
+        }
+    }
+    if ((rc = timed_launch(s, REPT_K_COMMIT, st, [&] { k_commit<<<grid, threads, 0, st>>>(s->d); }))) return rc;
+    if ((rc = timed_launch(s, REPT_K_INSERT, st, [&] { k_insert<<<grid, threads, 0, st>>>(s->d, b); }))) return rc;
+    const unsigned long long want_i = (n * 32 + 255) / 256;
+    const int grid_i = (int)std::min<unsigned long long>(want_i, (unsigned long long)s->grid_intersect);
+    const size_t smem = s->cfg.c * sizeof(unsigned long long);
+    if (s->cfg.flags & REPT_FLAG_WORK_COUNTERS)
+        rc = timed_launch(s, REPT_K_INTERSECT, st, [&] { k_intersect<true><<<grid_i, 256, smem, st>>>(s->d, b); });
+    else
+        rc = timed_launch(s, REPT_K_INTERSECT, st, [&] { k_intersect<false><<<grid_i, 256, smem, st>>>(s->d, b); });
+    if (rc) return rc;
+    s->next_t += n;
+    return REPT_OK;
+}
+
+int sync_status(rept_state* s, cudaStream_t st) {
+    int rc = read_ctrl(s, st);
+    if (rc) return rc;
+    return status_to_code(s->h_ctrl->status);
+}
+
+// f such that tau_hat = f * (integer sum): m^2 / c for c <= m, m / c1 for c = c1 * m.
+double estimate_factor(const rept_config& c) {
+    const double md = (double)c.m;
+    if (c.c <= c.m) return md * md / (double)c.c;
+    return md / (double)(c.c / c.m);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
+    if (!cfg || !out) return REPT_E_INVAL;
+    *out = nullptr;
+    if (cfg->m == 0 || cfg->c == 0 || cfg->n_nodes == 0 || cfg->n_nodes == 0xFFFFFFFFu) return REPT_E_INVAL;
+    if (cfg->c > cfg->m && cfg->c % cfg->m != 0) return REPT_E_INVAL;
+    if (cfg->c > kMaxProcessors) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    rept_state* s = new (std::nothrow) rept_state();
+    if (!s) return REPT_E_NOMEM;
+    s->cfg = *cfg;
+    int rc = REPT_OK;
+    auto fail = [&](int code) {
+        rept_destroy(s);
+        return code;
+    };
+    if (cudaGetDevice(&s->device) != cudaSuccess) return fail(REPT_E_CUDA);
+    if (cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess)
+        return fail(REPT_E_CUDA);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_intersect<false>, 256,
+                                                      cfg->c * sizeof(unsigned long long)) != cudaSuccess)
+        return fail(REPT_E_CUDA);
+    s->grid_intersect = s->sm_count * std::max(per_sm, 1);
+    s->grid_stream = s->sm_count * 8;
+    s->groups = cfg->c <= cfg->m ? 1u : cfg->c / cfg->m;
+    const uint32_t n = cfg->n_nodes;
+    StreamDev& d = s->d;
+    d.m = cfg->m;
+    d.c = cfg->c;
+    d.groups = s->groups;
+    d.n_nodes = n;
+    d.seed = cfg->seed;
+    const unsigned long long mb = cfg->max_batch ? cfg->max_batch : (1ull << 20);
+    unsigned long long quads = cfg->expected_edges ? quads_bound(cfg->expected_edges) : quads_bound(mb);
+    if (quads > 0xFFFFFFFFull) quads = 0xFFFFFFFFull;
+    if ((rc = dev_alloc(s, (void**)&d.meta, (size_t)n * sizeof(uint2)))) return fail(rc);
+    if ((rc = dev_alloc(s, (void**)&d.local, (size_t)n * sizeof(unsigned long long)))) return fail(rc);
+    if ((rc = dev_alloc(s, (void**)&d.proc, (size_t)cfg->c * sizeof(unsigned long long)))) return fail(rc);
+    if ((rc = dev_alloc(s, (void**)&d.add, (size_t)n * sizeof(uint32_t)))) return fail(rc);
+    if ((rc = dev_alloc(s, (void**)&d.ctrl, sizeof(Ctrl)))) return fail(rc);
+    if ((rc = dev_alloc(s, (void**)&d.pool, quads * 32ull))) return fail(rc);
+    if ((rc = dev_alloc(s, (void**)&s->d_global, sizeof(double)))) return fail(rc);
+    d.pool_quads = quads;
+    if ((rc = ensure_batch_scratch(s, mb, st))) return fail(rc);
+    if (cudaMallocHost((void**)&s->h_ctrl, sizeof(Ctrl)) != cudaSuccess) return fail(REPT_E_NOMEM);
+    if (cudaMallocHost((void**)&s->h_global, sizeof(double)) != cudaSuccess) return fail(REPT_E_NOMEM);
+    memset(s->h_ctrl, 0, sizeof(Ctrl));
+    if (cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return fail(REPT_E_CUDA);
+    if (cudaMemsetAsync(d.add, 0, (size_t)n * sizeof(uint32_t), st) != cudaSuccess) return fail(REPT_E_CUDA);
+    if (cudaMemsetAsync(d.pool, 0xFF, quads * 32ull, st) != cudaSuccess) return fail(REPT_E_CUDA);
+    if ((rc = rept_reset(s, stream))) return fail(rc);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(REPT_E_CUDA);
+    *out = s;
+    return REPT_OK;
+}
+
+int rept_reset(rept_state* s, void* stream) {
+    if (!s) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    StreamDev& d = s->d;
+    const size_t n = d.n_nodes;
+    // tables handed out so far go back to all-ones (empty)
+    REPT_CUDA(cudaMemcpyAsync(s->h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    REPT_CUDA(cudaStreamSynchronize(st));
+    unsigned long long used = s->h_ctrl->pool_top;
+    if (used > d.pool_quads) used = d.pool_quads;
+    if (used) REPT_CUDA(cudaMemsetAsync(d.pool, 0xFF, used * 32ull, st));
+    REPT_CUDA(cudaMemsetAsync(d.meta, 0, n * sizeof(uint2), st));
+    REPT_CUDA(cudaMemsetAsync(d.local, 0, n * sizeof(unsigned long long), st));
+    REPT_CUDA(cudaMemsetAsync(d.proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
+    REPT_CUDA(cudaMemsetAsync(d.add, 0, n * sizeof(uint32_t), st));
+    REPT_CUDA(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), st));
+    REPT_CUDA(cudaStreamSynchronize(st));
+    memset(s->h_ctrl, 0, sizeof(Ctrl));
+    s->next_t = 0;
+    return REPT_OK;
+}
+
+int rept_ingest_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n, void* stream) {
+    if (!s) return REPT_E_INVAL;
+    if (n == 0) return REPT_OK;
+    if (!d_src || !d_dst) return REPT_E_INVAL;
+    if (s->next_t + n >= 0xFFFFFFFFull) return REPT_E_INVAL;  // stream indices are 32-bit
+    cudaStream_t st = as_stream(stream);
+    int rc = ensure_batch_scratch(s, n, st);
+    if (rc) return rc;
+    rc = launch_batch(s, d_src, d_dst, n, st);
+    if (rc) return rc;
+    if (s->cfg.flags & REPT_FLAG_SYNC) return sync_status(s, st);
+    return REPT_OK;
+}
+
+int rept_ingest_host(rept_state* s, const uint32_t* h_src, const uint32_t* h_dst, uint64_t n, uint64_t batch,
+                     void* stream) {
+    if (!s) return REPT_E_INVAL;
+    if (n == 0) return REPT_OK;
+    if (!h_src || !h_dst) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    const unsigned long long chunk = batch ? batch : s->max_batch;
+    int rc = ensure_batch_scratch(s, chunk, st);
+    if (rc) return rc;
+    if (s->stage_cap < chunk) {
+        REPT_CUDA(cudaStreamSynchronize(st));
+        dev_free(s, s->stage_src, s->stage_cap * sizeof(uint32_t));
+        dev_free(s, s->stage_dst, s->stage_cap * sizeof(uint32_t));
+        s->stage_src = s->stage_dst = nullptr;
+        s->stage_cap = 0;
+        if ((rc = dev_alloc(s, (void**)&s->stage_src, chunk * sizeof(uint32_t)))) return rc;
+        if ((rc = dev_alloc(s, (void**)&s->stage_dst, chunk * sizeof(uint32_t)))) return rc;
+        s->stage_cap = chunk;
+    }
+    for (unsigned long long off = 0; off < n; off += chunk) {
+        const unsigned long long k = std::min<unsigned long long>(chunk, n - off);
+        REPT_CUDA(cudaMemcpyAsync(s->stage_src, h_src + off, k * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+        REPT_CUDA(cudaMemcpyAsync(s->stage_dst, h_dst + off, k * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+        if (s->next_t + k >= 0xFFFFFFFFull) return REPT_E_INVAL;
+        rc = launch_batch(s, s->stage_src, s->stage_dst, k, st);
+        if (rc) return rc;
+    }
+    REPT_CUDA(cudaStreamSynchronize(st));
+    if (s->cfg.flags & REPT_FLAG_SYNC) return sync_status(s, st);
+    return REPT_OK;
+}
+
+int rept_estimates(rept_state* s, double* h_global, double* d_local, void* stream) {
+    if (!s || !h_global) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    const double f = estimate_factor(s->cfg);
+    int rc0 = timed_launch(s, REPT_K_ESTIMATE, st,
+                           [&] { k_global_estimate<<<1, 256, 0, st>>>(s->d.proc, s->cfg.c, f, s->d_global); });
+    if (rc0) return rc0;
+    if (d_local) {
+        rc0 = timed_launch(s, REPT_K_ESTIMATE, st, [&] {
+            k_local_estimates<<<s->sm_count * 4, 256, 0, st>>>(s->d.local, s->d.n_nodes, f, d_local);
+        });
+        if (rc0) return rc0;
+    }
+    REPT_CUDA(cudaMemcpyAsync(s->h_global, s->d_global, sizeof(double), cudaMemcpyDeviceToHost, st));
+    int rc = sync_status(s, st);
+    *h_global = *s->h_global;
+    return rc;
+}
+
+int rept_estimates_host(rept_state* s, double* h_global, double* h_local, void* stream) {
+    if (!s || !h_global) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    double* dl = nullptr;
+    if (h_local) {
+        if (!s->d_local_tmp) {
+            int rc = dev_alloc(s, (void**)&s->d_local_tmp, (size_t)s->d.n_nodes * sizeof(double));
+            if (rc) return rc;
+        }
+        dl = s->d_local_tmp;
+    }
+    int rc = rept_estimates(s, h_global, dl, stream);
+    if (h_local) {
+        REPT_CUDA(cudaMemcpyAsync(h_local, dl, (size_t)s->d.n_nodes * sizeof(double), cudaMemcpyDeviceToHost, st));
+        REPT_CUDA(cudaStreamSynchronize(st));
+    }
+    return rc;
+}
+
+int rept_counts(rept_state* s, uint64_t* h_proc, uint64_t* d_local, void* stream) {
+    if (!s) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    if (h_proc)
+        REPT_CUDA(cudaMemcpyAsync(h_proc, s->d.proc, (size_t)s->cfg.c * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                  st));
+    if (d_local)
+        REPT_CUDA(cudaMemcpyAsync(d_local, s->d.local, (size_t)s->d.n_nodes * sizeof(uint64_t),
+                                  cudaMemcpyDeviceToDevice, st));
+    return sync_status(s, st);
+}
+
+int rept_get_stats(rept_state* s, rept_stats* out, void* stream) {
+    if (!s || !out) return REPT_E_INVAL;
+    int rc = sync_status(s, as_stream(stream));
+    out->edges = s->next_t;
+    out->self_loops = s->h_ctrl->self_loops;
+    out->stored_edges = s->h_ctrl->stored;
+    out->pool_slots = 4ull * s->d.pool_quads;
+    out->pool_used = 4ull * s->h_ctrl->pool_top;
+    out->device_bytes = s->device_bytes;
+    out->small_entries = s->h_ctrl->small_entries;
+    out->small_slots = s->h_ctrl->small_slots;
+    out->probes = s->h_ctrl->probes;
+    out->probe_slots = s->h_ctrl->probe_slots;
+    out->wedges = s->h_ctrl->wedges;
+    out->counted = s->h_ctrl->counted;
+    return rc;
+}
+
+int rept_kernel_times(rept_state* s, double* ms, uint64_t* launches, int clear) {
+    if (!s || !(s->cfg.flags & REPT_FLAG_PROFILE)) return REPT_E_INVAL;
+    int rc = fold_times(s);
+    if (rc) return rc;
+    for (int k = 0; k < REPT_NUM_KERNELS; ++k) {
+        if (ms) ms[k] = s->kernel_ms[k];
+        if (launches) launches[k] = s->kernel_launches[k];
+        if (clear) {
+            s->kernel_ms[k] = 0.0;
+            s->kernel_launches[k] = 0;
+        }
+    }
+    return REPT_OK;
+}
+
+int rept_sync(rept_state* s, void* stream) {
+    if (!s) return REPT_E_INVAL;
+    return sync_status(s, as_stream(stream));
+}
+
+void rept_destroy(rept_state* s) {
+    if (!s) return;
+    cudaDeviceSynchronize();
+    StreamDev& d = s->d;
+    cudaFree(d.meta);
+    cudaFree(d.local);
+    cudaFree(d.proc);
+    cudaFree(d.add);
+    cudaFree(d.ctrl);
+    cudaFree(d.pool);
+    cudaFree(d.touched);
+    cudaFree(d.grow_rel);
+    cudaFree(s->stage_src);
+    cudaFree(s->stage_dst);
+    cudaFree(s->d_global);
+    cudaFree(s->d_local_tmp);
+    for (auto& t : s->timed) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    for (auto e : s->spare_events) cudaEventDestroy(e);
+    if (s->h_ctrl) cudaFreeHost(s->h_ctrl);
+    if (s->h_global) cudaFreeHost(s->h_global);
+    delete s;
+}
+
+const char* rept_strerror(int code) {
+    switch (code) {
+        case REPT_OK: return "ok";
+        case REPT_E_INVAL: return "invalid argument";
+        case REPT_E_RANGE: return "edge endpoint >= n_nodes";
+        case REPT_E_CAPACITY: return "adjacency pool exhausted (fixed pool)";
+        case REPT_E_NOMEM: return "out of memory";
+        case REPT_E_CUDA: return "CUDA runtime error";
+        case REPT_E_TIMEOUT: return "bounded device wait timed out";
+        case REPT_E_INTERNAL: return "internal device invariant failed";
+        default: return "unknown error";
+    }
+}
+
+uint64_t rept_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Device-side data layout and helpers of the REPT streaming counter.
+//
+// HBM layout of one stream (one rept_state):
+//   meta[n_nodes]   uint2 {off, cnt}: node x's neighbour table starts at slot
+//                   4*off of the pool and holds cnt entries; its capacity is a
+//                   function of cnt alone (table_lg below), so a node's table
+//                   is re-allocated exactly when cnt crosses a power-of-two
+//                   boundary.
+//   pool[]          uint2 slots {nbr, eidx}: one open-addressing (linear
+//                   probing) table per node, keyed by the neighbour id.  An
+//                   entry (w, t) in x's table is the stored edge {x, w} that
+//                   arrived at stream index t.  Empty slots are all-ones.  The
+//                   tables of all processors share one union adjacency: an
+//                   edge is stored once if any processor keeps it, and which
+//                   processors keep it is recomputed from the hash when needed
+//                   (Section III-A: processor i keeps colour i).
+//   local[n_nodes]  uint64 sum over processors of tau_v^(i)
+//   proc[c]         uint64 tau^(i)
+// Per-batch scratch: add[n_nodes] (new entries per node, zero between
+// batches), touched[] (nodes with add > 0), grow_rel[] (their new table's
+// offset relative to this batch's allocation), and the control block.
+#pragma once
+
+#include <cstdint>
+
+namespace rept {
+
+constexpr uint32_t kEmptyId = 0xFFFFFFFFu;
+constexpr unsigned long long kEmptySlot = 0xFFFFFFFFFFFFFFFFull;
+constexpr uint64_t kGoldenGamma = 0x9E3779B97F4A7C15ull;  // SplitMix64 increment
+constexpr uint32_t kNoGrow = 0xFFFFFFFFu;
+constexpr uint32_t kMaxProcessors = 4096;  // per-block tau^(i) histogram lives in shared memory
+
+// status bits (sticky)
+constexpr unsigned kStRange = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeout = 8u;
+
+struct Ctrl {
+    unsigned long long n_touched;   // nodes in touched[] this batch
+    unsigned long long need_quads;  // table space requested by this batch, in 4-slot units
+    unsigned long long pool_top;    // 4-slot units handed out so far
+    unsigned long long self_loops;
+    unsigned long long stored;      // stored (kept) edges
+    unsigned int status;
+    unsigned int pad;
+    // work counters of k_intersect<true> (see rept_stats)
+    unsigned long long small_entries, small_slots, probes, probe_slots, wedges, counted;
+};
+
+// Everything a kernel needs to know about one stream's state.
+struct StreamDev {
+    uint32_t m, c, groups, n_nodes;
+    uint64_t seed;
+    uint2* meta;
+    uint2* pool;
+    unsigned long long pool_quads;
+    unsigned long long* local;
+    unsigned long long* proc;
+    uint32_t* add;
+    uint32_t* touched;
+    uint32_t* grow_rel;
+    Ctrl* ctrl;
+};
+
+// One batch of edges appended to a stream.
+struct BatchDev {
+    const uint32_t* src;
+    const uint32_t* dst;
+    unsigned long long n;
+    unsigned long long t0;  // stream index of src[0], dst[0]
+};
+
+// One output step of SplitMix64 from state x (Steele, Lea, Flood 2014).
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + kGoldenGamma;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// h_k({a, b}) given the group seed s_k.
+__device__ __forceinline__ uint32_t colour_of(uint32_t a, uint32_t b, uint64_t s_k, uint32_t m) {
+    uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    return (uint32_t)(splitmix64(((lo << 32) | hi) ^ s_k) % (uint64_t)m);
+}
+
+__device__ __forceinline__ uint64_t group_seed(uint64_t seed, uint32_t k) { return seed + (uint64_t)k * kGoldenGamma; }
+
+// Is edge {u, v} kept by some processor (k*m + h_k(u,v) < c for some group k)?
+__device__ __forceinline__ bool kept_by_any(const StreamDev& d, uint32_t u, uint32_t v) {
+    for (uint32_t k = 0; k < d.groups; ++k) {
+        uint32_t j = colour_of(u, v, group_seed(d.seed, k), d.m);
+        if (k * d.m + j < d.c) return true;
+    }
+    return false;
+}
+
+// log2 of the table capacity for cnt entries: capacity = max(4, nextpow2(2*cnt)); 0 when empty.
+__host__ __device__ __forceinline__ uint32_t table_lg(uint32_t cnt) {
+    if (cnt == 0) return 0;
+    uint32_t x = 2u * cnt - 1u;  // ceil(log2(2*cnt)) = bit length of (2*cnt - 1)
+#ifdef __CUDA_ARCH__
+    uint32_t lg = 32u - __clz(x);
+#else
+    uint32_t lg = 32u - (uint32_t)__builtin_clz(x);
+#endif
+    return lg < 2u ? 2u : lg;
+}
+
+// Home slot of neighbour w in a table of 2^lg slots (Fibonacci hashing).
+__device__ __forceinline__ uint32_t home_slot(uint32_t w, uint32_t lg) { return (w * 0x9E3779B1u) >> (32u - lg); }
+
+__device__ __forceinline__ unsigned long long pack_slot(uint32_t nbr, uint32_t eidx) {
+    return ((unsigned long long)eidx << 32) | nbr;
+}
+
+// Warp-aggregated atomicAdd: every active lane of the full warp calls it with its own
+// increment; returns the lane's exclusive offset from a single atomic per warp.
+__device__ __forceinline__ unsigned long long warp_reserve(unsigned long long* ctr, unsigned long long inc) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long incl = inc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (unsigned)o) incl += y;
+    }
+    unsigned long long total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total) base = atomicAdd(ctr, total);
+    base = __shfl_sync(0xFFFFFFFFu, base, 31);
+    return base + incl - inc;
+}
+
+}  // namespace rept

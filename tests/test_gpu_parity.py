@@ -1,0 +1,169 @@
+"""CUDA path vs the CPU oracle: bit-exact integer counts, FP64 estimates within 1e-12 relative.
+
+Every GPU call goes through the C-ABI (librept.so) via the ctypes binding.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_helpers import assert_counts_equal, assert_estimates_close, device_edges, gpu_run
+from paper_1811_09136_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+SUPPORTED_SMALL = [(2, 1), (2, 2), (3, 2), (4, 4), (5, 3), (2, 4), (3, 6), (1, 1), (1, 3), (7, 7)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("the GPU tests need a CUDA device")
+    from paper_1811_09136_gb300 import rept
+    rept.load()
+
+
+@pytest.mark.parametrize("n,q,gs", [(9, 0.7, 1), (23, 0.4, 2), (40, 0.3, 3)])
+@pytest.mark.parametrize("m,c", SUPPORTED_SMALL)
+def test_small_graphs_every_batch_split(n, q, gs, m, c):
+    s = gg.gnp(n, q, graph_seed=gs, order_seed=gs + 10)
+    ref = O.rept_stream(s.src, s.dst, n, m, c, 5)
+    ref_g, ref_loc = O.estimates(m, c, ref, n)
+    for batch in (1, 7, len(s)):
+        proc, local, g, loc, _ = gpu_run(s, m, c, 5, batch=batch)
+        assert_counts_equal(proc, local, ref.tau_proc, ref.local1, f"batch={batch}")
+        assert_estimates_close(g, loc, ref_g, ref_loc)
+
+
+def test_complete_graph_closed_form():
+    for n in (3, 4, 12, 64):
+        s = gg.complete(n, order_seed=n)
+        proc, local, g, loc, _ = gpu_run(s, 1, 1, 3, batch=5)
+        assert int(proc[0]) == math.comb(n, 3)
+        assert np.all(local == math.comb(n - 1, 2))
+        assert g == float(math.comb(n, 3))
+
+
+@pytest.mark.parametrize("m,c", [(10, 10), (10, 3), (4, 8), (1, 1)])
+def test_powerlaw_20k(m, c):
+    """Chung-Lu, 20,000 nodes, exponent 2.3, 200,000 edges: whole stream, 2^10 and 2^16 batches."""
+    s = gg.cached("powerlaw_20k")
+    ref = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, 1, pair_counters=False)
+    ref_g, ref_loc = O.estimates(m, c, ref, s.n_nodes)
+    for batch in (len(s), 1 << 10, 1 << 16):
+        proc, local, g, loc, st = gpu_run(s, m, c, 1, batch=batch)
+        assert_counts_equal(proc, local, ref.tau_proc, ref.local1, f"batch={batch}")
+        assert_estimates_close(g, loc, ref_g, ref_loc)
+        assert st["edges"] == len(s) and st["self_loops"] == 0
+
+
+def test_pool_growth_matches_presized_pool():
+    """A pool that starts small and grows gives the same counts as one sized up front."""
+    s = gg.chung_lu(30_000, 2.1, 150_000, graph_seed=5, order_seed=6)
+    a = gpu_run(s, 8, 8, 2, batch=4096, expected_edges=0, max_batch=4096)
+    b = gpu_run(s, 8, 8, 2, batch=4096, expected_edges=len(s))
+    assert_counts_equal(a[0], a[1], b[0], b[1])
+    assert a[4]["pool_slots"] < b[4]["pool_slots"] or a[4]["pool_slots"] >= a[4]["pool_used"]
+    ref = O.rept_stream(s.src, s.dst, s.n_nodes, 8, 8, 2, pair_counters=False)
+    assert_counts_equal(a[0], a[1], ref.tau_proc, ref.local1)
+
+
+def test_self_loops_skipped():
+    s = gg.gnp(30, 0.4, 7, 8)
+    src = np.insert(s.src, [3, 50, 50, len(s)], np.array([5, 9, 9, 2], dtype=np.uint32))
+    dst = np.insert(s.dst, [3, 50, 50, len(s)], np.array([5, 9, 9, 2], dtype=np.uint32))
+    loops = gg.EdgeStream(src, dst, 30)
+    ref = O.rept_stream(src, dst, 30, 3, 3, 4)
+    proc, local, _, _, st = gpu_run(loops, 3, 3, 4, batch=17)
+    assert_counts_equal(proc, local, ref.tau_proc, ref.local1)
+    assert st["self_loops"] == 4 == ref.skipped
+
+
+def test_empty_batch_and_ingest_host_equal_device():
+    from paper_1811_09136_gb300.rept import ReptStream
+    import torch
+    s = gg.chung_lu(5000, 2.3, 40_000, graph_seed=9, order_seed=10)
+    with ReptStream(s.n_nodes, 5, 5, 11) as r:
+        empty = torch.empty(0, dtype=torch.int32, device="cuda")
+        r.ingest(empty, empty)
+        r.ingest_host(s.src, s.dst, batch=3000)
+        proc, local = r.counts()
+        st = r.stats()
+    ref = O.rept_stream(s.src, s.dst, s.n_nodes, 5, 5, 11, pair_counters=False)
+    assert_counts_equal(proc, local.cpu().numpy().view(np.uint64), ref.tau_proc, ref.local1)
+    assert st["edges"] == len(s)
+
+
+def test_range_error_leaves_state_unchanged_and_reset_recovers():
+    from paper_1811_09136_gb300.rept import ReptStream, ReptError
+    import torch
+    s = gg.gnp(40, 0.3, 12, 13)
+    half = len(s) // 2
+    src, dst = device_edges(s)
+    with ReptStream(s.n_nodes, 3, 3, 1) as r:
+        r.ingest(src[:half], dst[:half])
+        bad = torch.tensor([1, 40, 2], dtype=torch.int32, device="cuda")  # 40 >= n_nodes
+        ok = torch.tensor([2, 3, 4], dtype=torch.int32, device="cuda")
+        r.ingest(ok, bad)
+        r.ingest(src[half:], dst[half:])  # also dropped: the error is sticky
+        proc, local, rc = r.counts(allow_error=True)
+        assert rc == -2
+        with pytest.raises(ReptError):
+            r.sync()
+        ref = O.rept_stream(s.src[:half], s.dst[:half], 40, 3, 3, 1)
+        assert_counts_equal(proc, local.cpu().numpy().view(np.uint64), ref.tau_proc, ref.local1)
+        r.reset()
+        r.ingest(src, dst)
+        proc, local = r.counts()
+        full = O.rept_stream(s.src, s.dst, 40, 3, 3, 1)
+        assert_counts_equal(proc, local.cpu().numpy().view(np.uint64), full.tau_proc, full.local1)
+
+
+def test_fixed_pool_capacity_error():
+    from paper_1811_09136_gb300.rept import ReptStream, FLAG_FIXED_POOL
+    s = gg.chung_lu(20_000, 2.2, 100_000, graph_seed=14, order_seed=15)
+    src, dst = device_edges(s)
+    # pool sized for 2,000 edges: the first batch fits, a later one cannot
+    with ReptStream(s.n_nodes, 4, 4, 3, expected_edges=2000, max_batch=1000, flags=FLAG_FIXED_POOL) as r:
+        r.ingest(src[:1000], dst[:1000])
+        r.sync()
+        good = r.counts()
+        for off in range(1000, len(s), 1000):
+            r.ingest(src[off:off + 1000], dst[off:off + 1000])
+        proc, local, rc = r.counts(allow_error=True)
+        assert rc == -3
+    # counts are those of a prefix that ended at a batch boundary, and never exceed the full stream's
+    ref_full = O.rept_stream(s.src, s.dst, s.n_nodes, 4, 4, 3, pair_counters=False)
+    assert int(proc.sum()) <= int(ref_full.tau_proc.sum())
+    assert int(proc.sum()) >= int(good[0].sum())
+    found = False
+    for end in range(1000, len(s) + 1, 1000):
+        ref = O.rept_stream(s.src[:end], s.dst[:end], s.n_nodes, 4, 4, 3, pair_counters=False)
+        if np.array_equal(ref.tau_proc, proc):
+            assert_counts_equal(proc, local.cpu().numpy().view(np.uint64), ref.tau_proc, ref.local1)
+            found = True
+            break
+        if int(ref.tau_proc.sum()) > int(proc.sum()):
+            break
+    assert found
+
+
+def test_large_node_ids():
+    """Ids near the top of a 2^27-node space (meta/local arrays of 1-2 GB)."""
+    n = 1 << 27
+    base = gg.gnp(60, 0.25, 16, 17)
+    off = np.uint32(n - 64)
+    s = gg.EdgeStream(base.src + off, base.dst + off, n)
+    proc, local, g, loc, _ = gpu_run(s, 3, 3, 8, batch=37)
+    ref = O.rept_stream(base.src, base.dst, 60, 3, 3, 8)
+    assert np.array_equal(proc, ref.tau_proc)
+    assert np.array_equal(local[n - 64: n - 4], ref.local1)
+    assert int(local[: n - 64].sum()) == 0
+
+
+def test_unsupported_partial_group_rejected():
+    from paper_1811_09136_gb300.rept import ReptStream, ReptError
+    with pytest.raises(ReptError):
+        ReptStream(100, 3, 7, 1)
