@@ -128,12 +128,16 @@ int ensure_batch_scratch(rept_state* s, unsigned long long n, cudaStream_t st) {
     const unsigned long long old = s->max_batch;
     dev_free(s, s->d.touched, 2 * old * sizeof(uint32_t));
     dev_free(s, s->d.grow_rel, 2 * old * sizeof(uint32_t));
+    dev_free(s, s->d.bins, kBins * old * sizeof(uint32_t));
     s->d.touched = nullptr;
     s->d.grow_rel = nullptr;
+    s->d.bins = nullptr;
     int rc = dev_alloc(s, (void**)&s->d.touched, 2 * n * sizeof(uint32_t));
     if (!rc) rc = dev_alloc(s, (void**)&s->d.grow_rel, 2 * n * sizeof(uint32_t));
+    if (!rc) rc = dev_alloc(s, (void**)&s->d.bins, kBins * n * sizeof(uint32_t));
     if (rc) return rc;
     s->max_batch = n;
+    s->d.bin_cap = n;
     return REPT_OK;
 }
 
@@ -206,7 +210,7 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
     }
     if ((rc = timed_launch(s, REPT_K_COMMIT, st, [&] { k_commit<<<grid, threads, 0, st>>>(s->d); }))) return rc;
     if ((rc = timed_launch(s, REPT_K_INSERT, st, [&] { k_insert<<<grid, threads, 0, st>>>(s->d, b); }))) return rc;
-    const unsigned long long want_i = (n * 32 + 255) / 256;
+    const unsigned long long want_i = (n * 8 + 255) / 256;  // work is claimed dynamically; >= 1 block
     const int grid_i = (int)std::min<unsigned long long>(want_i, (unsigned long long)s->grid_intersect);
     const size_t smem = s->cfg.c * sizeof(unsigned long long);
     if (s->cfg.flags & REPT_FLAG_WORK_COUNTERS)
@@ -459,6 +463,7 @@ void rept_destroy(rept_state* s) {
     cudaFree(d.pool);
     cudaFree(d.touched);
     cudaFree(d.grow_rel);
+    cudaFree(d.bins);
     cudaFree(s->stage_src);
     cudaFree(s->stage_dst);
     cudaFree(s->d_global);

@@ -30,6 +30,10 @@ constexpr unsigned long long kEmptySlot = 0xFFFFFFFFFFFFFFFFull;
 constexpr uint64_t kGoldenGamma = 0x9E3779B97F4A7C15ull;  // SplitMix64 increment
 constexpr uint32_t kNoGrow = 0xFFFFFFFFu;
 constexpr uint32_t kMaxProcessors = 4096;  // per-block tau^(i) histogram lives in shared memory
+// k_intersect work classes by the smaller endpoint's table size 2^lg: lg 2..5 are handled by
+// tiles of 4, 8, 16, 32 lanes (one slot per lane), 64..512 slots and >= 1024 slots by a warp.
+constexpr int kBins = 6;
+__host__ __device__ __forceinline__ int bin_of(uint32_t lg_s) { return lg_s <= 5u ? (int)lg_s - 2 : (lg_s <= 9u ? 4 : 5); }
 
 // status bits (sticky)
 constexpr unsigned kStRange = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeout = 8u;
@@ -44,6 +48,9 @@ struct Ctrl {
     unsigned int pad;
     // work counters of k_intersect<true> (see rept_stats)
     unsigned long long small_entries, small_slots, probes, probe_slots, wedges, counted;
+    // per-batch work lists of k_intersect: items appended by k_insert, claimed by k_intersect
+    unsigned long long bin_count[kBins];
+    unsigned long long bin_next[kBins];
 };
 
 // Everything a kernel needs to know about one stream's state.
@@ -58,6 +65,8 @@ struct StreamDev {
     uint32_t* add;
     uint32_t* touched;
     uint32_t* grow_rel;
+    uint32_t* bins;  // kBins lists of bin_cap edge indices (batch-relative)
+    unsigned long long bin_cap;
     Ctrl* ctrl;
 };
 

@@ -36,6 +36,10 @@ __device__ __forceinline__ bool table_insert(uint2* pool, unsigned long long bas
 }
 
 __global__ void k_classify(StreamDev d, BatchDev b) {
+    if (blockIdx.x == 0 && threadIdx.x < kBins) {  // the previous batch's work lists are consumed
+        d.ctrl->bin_count[threadIdx.x] = 0ull;
+        d.ctrl->bin_next[threadIdx.x] = 0ull;
+    }
     if (d.ctrl->status) return;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -139,12 +143,26 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
         if (valid) { u = b.src[e]; v = b.dst[e]; }
         const bool loop = valid && u == v;
         const bool kept = valid && u != v && kept_by_any(d, u, v);
-        if (kept) {
-            const uint32_t t = (uint32_t)(b.t0 + e);
+        int cls = -1;
+        if (valid && u != v) {
             const uint2 mu = d.meta[u], mv = d.meta[v];
-            bool ok = table_insert(d.pool, 4ull * mu.x, table_lg(mu.y), v, t);
-            ok &= table_insert(d.pool, 4ull * mv.x, table_lg(mv.y), u, t);
-            if (!ok) atomicOr(&ct->status, kStInternal);
+            if (kept) {
+                const uint32_t t = (uint32_t)(b.t0 + e);
+                bool ok = table_insert(d.pool, 4ull * mu.x, table_lg(mu.y), v, t);
+                ok &= table_insert(d.pool, 4ull * mv.x, table_lg(mv.y), u, t);
+                if (!ok) atomicOr(&ct->status, kStInternal);
+            }
+            // an edge can close wedges only if both endpoints have stored edges
+            if (mu.y != 0u && mv.y != 0u) cls = bin_of(table_lg(mu.y <= mv.y ? mu.y : mv.y));
+        }
+        for (int k = 0; k < kBins; ++k) {
+            const unsigned mask = __ballot_sync(0xFFFFFFFFu, cls == k);
+            if (mask == 0u) continue;
+            const int leader = __ffs(mask) - 1;
+            unsigned long long pos = 0;
+            if ((int)lane == leader) pos = atomicAdd(&ct->bin_count[k], (unsigned long long)__popc(mask));
+            pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+            if (cls == k) d.bins[k * d.bin_cap + pos + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)e;
         }
         warp_reserve(&ct->self_loops, loop ? 1ull : 0ull);
         warp_reserve(&ct->stored, kept ? 1ull : 0ull);
@@ -167,82 +185,214 @@ __device__ __forceinline__ uint32_t table_find(const uint2* __restrict__ pool, u
     return kEmptyId;
 }
 
-// One warp per arriving edge.  Dynamic shared memory: c uint64 counters (tau^(i) of this block).
-// WORK = true also tallies the table reads into the control block (for the roofline's byte count).
+// Work counters of k_intersect<true>, kept per lane in registers.
+struct Work {
+    unsigned long long entries = 0, slots = 0, probes = 0, pslots = 0, wedges = 0, counted = 0;
+};
+
+// Wedge (s, w), (l, w), both edges older than the arriving edge (s, l): count it for every hash group
+// whose colour of the two edges agrees and names a kept processor.  Returns the number of groups.
+__device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, uint32_t l, uint32_t w,
+                                                unsigned long long* s_proc) {
+    uint32_t found = 0;
+    for (uint32_t k = 0; k < d.groups; ++k) {
+        const uint64_t sk = group_seed(d.seed, k);
+        const uint32_t js = colour_of(s, w, sk, d.m);
+        if (k * d.m + js < d.c && colour_of(l, w, sk, d.m) == js) {
+            ++found;
+            atomicAdd(&s_proc[k * d.m + js], 1ull);
+        }
+    }
+    if (found) atomicAdd(&d.local[w], (unsigned long long)found);
+    return found;
+}
+
+// The endpoints of edge e in the order (smaller table, larger table); false if either table is empty.
+struct EdgeView {
+    uint32_t u, v, s, l, t;
+    uint2 ms, ml;
+};
+
+__device__ __forceinline__ EdgeView edge_view(const StreamDev& d, const BatchDev& b, uint32_t e) {
+    EdgeView x;
+    x.u = b.src[e];
+    x.v = b.dst[e];
+    x.t = (uint32_t)(b.t0 + e);
+    const uint2 mu = d.meta[x.u], mv = d.meta[x.v];
+    const bool u_small = mu.y <= mv.y;
+    x.s = u_small ? x.u : x.v;
+    x.l = u_small ? x.v : x.u;
+    x.ms = u_small ? mu : mv;
+    x.ml = u_small ? mv : mu;
+    return x;
+}
+
+// Edges whose smaller table has exactly TILE slots: one tile of TILE lanes per edge, one slot per lane.
+template <int TILE, bool WORK>
+__device__ __forceinline__ void intersect_tile(const StreamDev& d, const BatchDev& b, uint32_t e, bool valid,
+                                               unsigned long long* s_proc, Work& wk) {
+    const unsigned lane = threadIdx.x & 31u, j = lane & (TILE - 1);
+    uint32_t found = 0;
+    EdgeView x{};
+    if (valid) {
+        x = edge_view(d, b, e);
+        const uint2 es = d.pool[4ull * x.ms.x + j];
+        if (WORK && j == 0) { wk.entries += x.ms.y; wk.slots += TILE; }
+        if (es.x != kEmptyId && es.y < x.t) {
+            uint32_t nslots = 0;
+            const uint32_t tl = table_find(d.pool, 4ull * x.ml.x, table_lg(x.ml.y), es.x, nslots);
+            if (WORK) { ++wk.probes; wk.pslots += nslots; }
+            if (tl < x.t) {  // kEmptyId (absent) is never < t
+                found = count_wedge(d, x.s, x.l, es.x, s_proc);
+                if (WORK) { ++wk.wedges; wk.counted += found; }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = TILE / 2; o > 0; o >>= 1) found += __shfl_xor_sync(0xFFFFFFFFu, found, o);
+    if (valid && j == 0 && found) {
+        atomicAdd(&d.local[x.u], (unsigned long long)found);
+        atomicAdd(&d.local[x.v], (unsigned long long)found);
+    }
+}
+
+// Two probes of the same table interleaved, so that each lane keeps two loads in flight.
+__device__ __forceinline__ void table_find2(const uint2* __restrict__ pool, unsigned long long base, uint32_t lg,
+                                            uint32_t w1, bool a1, uint32_t w2, bool a2, uint32_t& r1, uint32_t& r2,
+                                            uint32_t& slots) {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h1 = home_slot(w1, lg), h2 = home_slot(w2, lg);
+    bool d1 = !a1, d2 = !a2;
+    r1 = kEmptyId;
+    r2 = kEmptyId;
+    slots = 0;
+    for (uint32_t probe = 0; probe <= mask && !(d1 && d2); ++probe) {
+        uint2 s1 = make_uint2(kEmptyId, kEmptyId), s2 = s1;
+        if (!d1) s1 = pool[base + h1];
+        if (!d2) s2 = pool[base + h2];
+        if (!d1) {
+            ++slots;
+            if (s1.x == w1) { r1 = s1.y; d1 = true; }
+            else if (s1.x == kEmptyId) d1 = true;
+            else h1 = (h1 + 1u) & mask;
+        }
+        if (!d2) {
+            ++slots;
+            if (s2.x == w2) { r2 = s2.y; d2 = true; }
+            else if (s2.x == kEmptyId) d2 = true;
+            else h2 = (h2 + 1u) & mask;
+        }
+    }
+}
+
+// Edges whose smaller table has >= 64 slots: a warp per edge, two slots per lane per 16-byte load.
+template <bool WORK>
+__device__ __forceinline__ void intersect_warp(const StreamDev& d, const BatchDev& b, uint32_t e,
+                                               unsigned long long* s_proc, Work& wk) {
+    const unsigned lane = threadIdx.x & 31u;
+    const EdgeView x = edge_view(d, b, e);
+    const uint32_t cap_s = 1u << table_lg(x.ms.y), lg_l = table_lg(x.ml.y);
+    const unsigned long long base_s = 4ull * x.ms.x, base_l = 4ull * x.ml.x;
+    if (WORK && lane == 0) { wk.entries += x.ms.y; wk.slots += cap_s; }
+    const uint4* tab = reinterpret_cast<const uint4*>(d.pool + base_s);  // 32-byte aligned table
+    uint32_t total = 0;
+    for (uint32_t j0 = 0; j0 < cap_s; j0 += 64u) {
+        const uint4 q = tab[(j0 >> 1) + lane];
+        const bool a1 = q.x != kEmptyId && q.y < x.t, a2 = q.z != kEmptyId && q.w < x.t;
+        uint32_t found = 0;
+        if (a1 || a2) {
+            uint32_t r1, r2, nslots;
+            table_find2(d.pool, base_l, lg_l, q.x, a1, q.z, a2, r1, r2, nslots);
+            if (WORK) { wk.probes += (uint32_t)a1 + (uint32_t)a2; wk.pslots += nslots; }
+            if (r1 < x.t) {
+                const uint32_t f = count_wedge(d, x.s, x.l, q.x, s_proc);
+                found += f;
+                if (WORK) { ++wk.wedges; wk.counted += f; }
+            }
+            if (r2 < x.t) {
+                const uint32_t f = count_wedge(d, x.s, x.l, q.z, s_proc);
+                found += f;
+                if (WORK) { ++wk.wedges; wk.counted += f; }
+            }
+        }
+        total += __reduce_add_sync(0xFFFFFFFFu, found);
+    }
+    if (lane == 0 && total) {
+        atomicAdd(&d.local[x.u], (unsigned long long)total);
+        atomicAdd(&d.local[x.v], (unsigned long long)total);
+    }
+}
+
+template <int TILE, bool WORK>
+__device__ __forceinline__ void drain_tile_bin(const StreamDev& d, const BatchDev& b, int cls,
+                                               unsigned long long* s_proc, Work& wk) {
+    constexpr uint32_t kPerWarp = 32 / TILE, kRounds = 4, kGrab = kPerWarp * kRounds;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long count = d.ctrl->bin_count[cls];
+    const uint32_t* items = d.bins + (unsigned long long)cls * d.bin_cap;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&d.ctrl->bin_next[cls], (unsigned long long)kGrab);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= count) break;
+#pragma unroll 1
+        for (uint32_t r = 0; r < kRounds; ++r) {
+            const unsigned long long i = base + r * kPerWarp + lane / TILE;
+            const bool valid = i < count;
+            intersect_tile<TILE, WORK>(d, b, valid ? items[i] : 0u, valid, s_proc, wk);
+        }
+    }
+}
+
+template <bool WORK>
+__device__ __forceinline__ void drain_warp_bin(const StreamDev& d, const BatchDev& b, int cls,
+                                               unsigned long long* s_proc, Work& wk) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long count = d.ctrl->bin_count[cls];
+    const uint32_t* items = d.bins + (unsigned long long)cls * d.bin_cap;
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(&d.ctrl->bin_next[cls], 1ull);
+        i = __shfl_sync(0xFFFFFFFFu, i, 0);
+        if (i >= count) break;
+        intersect_warp<WORK>(d, b, items[i], s_proc, wk);
+    }
+}
+
+// UpdateTriangleCNT for every edge of the batch.  The edges were sorted into work classes by
+// k_insert; warps claim work dynamically, largest class first.  Dynamic shared memory: c uint64
+// counters (tau^(i) of this block).  WORK = true also tallies the table reads.
 template <bool WORK>
 __global__ void __launch_bounds__(256) k_intersect(StreamDev d, BatchDev b) {
     extern __shared__ unsigned long long s_proc[];
     for (uint32_t i = threadIdx.x; i < d.c; i += blockDim.x) s_proc[i] = 0ull;
     __syncthreads();
-    const unsigned status = d.ctrl->status;
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    unsigned long long w_entries = 0, w_slots = 0, w_probes = 0, w_pslots = 0, w_wedges = 0, w_counted = 0;
-    if (status == 0u) {
-        for (unsigned long long e = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < b.n;
-             e += warps) {
-            const uint32_t u = b.src[e], v = b.dst[e];
-            if (u == v) continue;
-            const uint32_t t = (uint32_t)(b.t0 + e);
-            const uint2 mu = d.meta[u], mv = d.meta[v];
-            if (mu.y == 0u || mv.y == 0u) continue;
-            const bool u_small = mu.y <= mv.y;
-            const uint32_t s = u_small ? u : v, l = u_small ? v : u;
-            const uint2 ms = u_small ? mu : mv, ml = u_small ? mv : mu;
-            const uint32_t cap_s = 1u << table_lg(ms.y);
-            const uint32_t lg_l = table_lg(ml.y);
-            const unsigned long long base_s = 4ull * ms.x, base_l = 4ull * ml.x;
-            if (WORK && lane == 0) { w_entries += ms.y; w_slots += cap_s; }
-            uint32_t total = 0;
-            for (uint32_t j0 = 0; j0 < cap_s; j0 += 32u) {
-                const uint32_t j = j0 + lane;
-                uint32_t found = 0;  // groups in which this wedge counts
-                if (j < cap_s) {
-                    const uint2 es = d.pool[base_s + j];
-                    if (es.x != kEmptyId && es.y < t) {
-                        uint32_t nslots = 0;
-                        const uint32_t tl = table_find(d.pool, base_l, lg_l, es.x, nslots);
-                        if (WORK) { ++w_probes; w_pslots += nslots; }
-                        if (tl < t) {  // kEmptyId (absent) is never < t
-                            const uint32_t w = es.x;
-                            if (WORK) ++w_wedges;
-                            for (uint32_t k = 0; k < d.groups; ++k) {
-                                const uint64_t sk = group_seed(d.seed, k);
-                                const uint32_t js = colour_of(s, w, sk, d.m);
-                                if (k * d.m + js < d.c && colour_of(l, w, sk, d.m) == js) {
-                                    ++found;
-                                    atomicAdd(&s_proc[k * d.m + js], 1ull);
-                                }
-                            }
-                            if (found) atomicAdd(&d.local[w], (unsigned long long)found);
-                            if (WORK) w_counted += found;
-                        }
-                    }
-                }
-                total += __reduce_add_sync(0xFFFFFFFFu, found);
-            }
-            if (lane == 0 && total) {
-                atomicAdd(&d.local[u], (unsigned long long)total);
-                atomicAdd(&d.local[v], (unsigned long long)total);
-            }
-        }
+    Work wk;
+    if (d.ctrl->status == 0u) {
+        drain_warp_bin<WORK>(d, b, 5, s_proc, wk);
+        drain_warp_bin<WORK>(d, b, 4, s_proc, wk);
+        drain_tile_bin<32, WORK>(d, b, 3, s_proc, wk);
+        drain_tile_bin<16, WORK>(d, b, 2, s_proc, wk);
+        drain_tile_bin<8, WORK>(d, b, 1, s_proc, wk);
+        drain_tile_bin<4, WORK>(d, b, 0, s_proc, wk);
     }
     if (WORK) {
         for (int o = 16; o > 0; o >>= 1) {
-            w_entries += __shfl_down_sync(0xFFFFFFFFu, w_entries, o);
-            w_slots += __shfl_down_sync(0xFFFFFFFFu, w_slots, o);
-            w_probes += __shfl_down_sync(0xFFFFFFFFu, w_probes, o);
-            w_pslots += __shfl_down_sync(0xFFFFFFFFu, w_pslots, o);
-            w_wedges += __shfl_down_sync(0xFFFFFFFFu, w_wedges, o);
-            w_counted += __shfl_down_sync(0xFFFFFFFFu, w_counted, o);
+            wk.entries += __shfl_down_sync(0xFFFFFFFFu, wk.entries, o);
+            wk.slots += __shfl_down_sync(0xFFFFFFFFu, wk.slots, o);
+            wk.probes += __shfl_down_sync(0xFFFFFFFFu, wk.probes, o);
+            wk.pslots += __shfl_down_sync(0xFFFFFFFFu, wk.pslots, o);
+            wk.wedges += __shfl_down_sync(0xFFFFFFFFu, wk.wedges, o);
+            wk.counted += __shfl_down_sync(0xFFFFFFFFu, wk.counted, o);
         }
         if (lane == 0) {
-            atomicAdd(&d.ctrl->small_entries, w_entries);
-            atomicAdd(&d.ctrl->small_slots, w_slots);
-            atomicAdd(&d.ctrl->probes, w_probes);
-            atomicAdd(&d.ctrl->probe_slots, w_pslots);
-            atomicAdd(&d.ctrl->wedges, w_wedges);
-            atomicAdd(&d.ctrl->counted, w_counted);
+            atomicAdd(&d.ctrl->small_entries, wk.entries);
+            atomicAdd(&d.ctrl->small_slots, wk.slots);
+            atomicAdd(&d.ctrl->probes, wk.probes);
+            atomicAdd(&d.ctrl->probe_slots, wk.pslots);
+            atomicAdd(&d.ctrl->wedges, wk.wedges);
+            atomicAdd(&d.ctrl->counted, wk.counted);
         }
     }
     __syncthreads();

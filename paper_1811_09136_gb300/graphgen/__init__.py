@@ -13,6 +13,7 @@ import ctypes
 import hashlib
 import os
 import subprocess
+import tempfile
 import threading
 
 import numpy as np
@@ -163,7 +164,7 @@ def powerlaw_4m() -> EdgeStream:
     return chung_lu(1 << 22, 2.1, 64 << 20, cap=50_000.0)
 
 
-_CACHE_DIR = os.environ.get("REPT_STREAM_CACHE", os.path.join(os.path.dirname(os.path.dirname(_HERE)), "_cache"))
+_CACHE_DIR = os.environ.get("REPT_STREAM_CACHE", os.path.join(tempfile.gettempdir(), "rept_stream_cache"))
 
 
 def cached(name: str) -> EdgeStream:
