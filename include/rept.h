@@ -56,6 +56,7 @@ extern "C" {
 #define REPT_E_CUDA (-5)      /* a CUDA runtime call failed */
 #define REPT_E_TIMEOUT (-6)   /* a bounded device-side wait gave up (batched persistent path) */
 #define REPT_E_INTERNAL (-7)  /* a device-side invariant failed (bounded probe found no slot) */
+#define REPT_E_SCRATCH (-8)   /* rept_count_noalloc: the problem does not fit its fixed scratch area */
 
 #define REPT_FLAG_FIXED_POOL 1u /* never grow the adjacency pool; a full pool gives REPT_E_CAPACITY */
 #define REPT_FLAG_SYNC 2u       /* synchronise at the end of every ingest and report errors at once */
@@ -175,6 +176,45 @@ int rept_sync(rept_state* s, void* stream);
 
 /* rept_destroy: free every allocation of the handle (NULL is a no-op).  Waits for the handle's pending work. */
 void rept_destroy(rept_state* s);
+
+/*
+ * rept_count_noalloc: count a whole edge stream in one call without
+ * allocating any memory.  The paper has no counterpart; this is a library
+ * convenience for callers that cannot call cudaMalloc -- for example code
+ * whose device memory is entirely owned by another allocator (a framework's
+ * caching allocator that has reserved the free memory), or a latency-critical
+ * loop that cannot afford the device-wide synchronisation that cudaFree
+ * implies.  It computes the same counts as rept_create + one
+ * rept_ingest_batch of all n_edges edges + rept_counts, and the same global
+ * estimate as rept_estimates.
+ *
+ * Scratch: all intermediate state (per-node tables, batch work lists, the
+ * control block) lives in one statically allocated device array of
+ * REPT_NOALLOC_SCRATCH_BYTES (64 MiB) inside this library; every GPU that
+ * loads the library holds that array until the process exits.  A problem
+ * needs 12 * n_nodes + 104 * n_edges + 8 KiB bytes of it (for example
+ * 2^20 nodes and 500,000 edges); larger problems return REPT_E_SCRATCH
+ * before any device work is enqueued.  c must be at most 4096.
+ *
+ * Arguments: d_src / d_dst: device arrays of n_edges uint32 endpoints
+ * (self-loops skipped as in rept_ingest_batch).  Outputs, caller-allocated on
+ * the same device and overwritten: d_proc[c] (tau^(i), uint64), d_local[n_nodes]
+ * (sum_i tau_v^(i), uint64), d_global (tau_hat, one double; may be NULL).
+ * m, c, seed, n_nodes have the meaning of rept_config; c > m needs c % m == 0.
+ *
+ * Behaviour: the first call on a device looks up the scratch array's device
+ * address on that device (cudaGetSymbolAddress) and caches it; make that first
+ * call before any stream capture.  Every call enqueues its work on `stream`,
+ * then waits for the stream and returns REPT_E_RANGE if an endpoint was
+ * >= n_nodes (outputs then undefined).  All calls share the one scratch array
+ * and the call clears the parts that must start at zero, so sequential calls
+ * are independent; calls whose work overlaps on the GPU (other host threads,
+ * other streams) race on the scratch and give undefined results.
+ */
+#define REPT_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, uint64_t n_edges, uint32_t n_nodes, uint32_t m,
+                       uint32_t c, uint64_t seed, uint64_t* d_proc, uint64_t* d_local, double* d_global,
+                       void* stream);
 
 /* rept_strerror: static English text for a REPT_* code. */
 const char* rept_strerror(int code);

@@ -33,7 +33,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
             return LIB_PATH
     tmp = LIB_PATH + f".tmp{os.getpid()}"
     cmd = [_nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-I", CSRC, "-shared", "-o", tmp,
-           os.path.join(CSRC, "rept_api.cu")]
+           *sorted(glob.glob(os.path.join(CSRC, "*.cu")))]
     if verbose_ptxas:
         cmd[1:1] = ["-Xptxas", "-v"]
     subprocess.check_call(cmd)

@@ -488,6 +488,7 @@ const char* rept_strerror(int code) {
         case REPT_E_CUDA: return "CUDA runtime error";
         case REPT_E_TIMEOUT: return "bounded device wait timed out";
         case REPT_E_INTERNAL: return "internal device invariant failed";
+        case REPT_E_SCRATCH: return "problem exceeds the fixed scratch area of rept_count_noalloc";
         default: return "unknown error";
     }
 }

@@ -19,6 +19,8 @@
 #include "rept_common.cuh"
 
 namespace rept {
+// Internal linkage: every translation unit of the library that launches these kernels gets its own copy.
+namespace {
 
 // Insert (nbr, eidx) into the table of 2^lg slots starting at slot `base`.  Returns false
 // only if the table has no empty slot left (impossible while cnt <= capacity / 2).
@@ -423,4 +425,5 @@ __global__ void k_global_estimate(const unsigned long long* __restrict__ proc, u
     }
 }
 
+}  // namespace
 }  // namespace rept

@@ -1,0 +1,147 @@
+// rept_count_noalloc (include/rept.h): the whole counting path for one stream, with every piece of
+// intermediate state carved out of one file-scope device array instead of cudaMalloc.  The kernels
+// are the library's batch kernels, run once over all edges as a single batch on an empty state.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstring>
+
+#include "rept.h"
+#include "rept_common.cuh"
+#include "rept_kernels.cuh"
+
+using namespace rept;
+
+namespace {
+
+// The scratch area.  In host code `g_scratch` names a host-side stand-in, not device memory: the
+// kernels get the device address looked up below.
+static __device__ __align__(256) unsigned char g_scratch[REPT_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::atomic<void*> g_scratch_addr[kMaxDevices];  // device address of g_scratch, per device
+
+inline unsigned long long align256(unsigned long long x) { return (x + 255ull) & ~255ull; }
+
+// Offsets of the state inside the scratch area for n nodes and E edges.
+struct Layout {
+    unsigned long long meta, add, touched, grow_rel, bins, ctrl, pool, end;
+    unsigned long long pool_quads;
+};
+
+Layout layout_for(unsigned long long n, unsigned long long E) {
+    Layout L{};
+    unsigned long long o = 0;
+    L.meta = o;     o = align256(o + n * sizeof(uint2));
+    L.add = o;      o = align256(o + n * sizeof(uint32_t));
+    L.touched = o;  o = align256(o + 2 * E * sizeof(uint32_t));
+    L.grow_rel = o; o = align256(o + 2 * E * sizeof(uint32_t));
+    L.bins = o;     o = align256(o + (unsigned long long)kBins * E * sizeof(uint32_t));
+    L.ctrl = o;     o = align256(o + sizeof(Ctrl));
+    // From an empty state every node's table is allocated once, with at most 4 slots per entry:
+    // at most 8 slots (2 quads) per edge.
+    L.pool_quads = 2 * E + 1;
+    L.pool = o;     o = align256(o + L.pool_quads * 32ull);
+    L.end = o;
+    return L;
+}
+
+int scratch_address(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return REPT_E_CUDA;
+    void* p = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        // set-up, once per device, with that device current
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return REPT_E_CUDA;
+        }
+        g_scratch_addr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return REPT_OK;
+}
+
+#define NA_CUDA(call)                          \
+    do {                                       \
+        if ((call) != cudaSuccess) {           \
+            (void)cudaGetLastError();          \
+            return REPT_E_CUDA;                \
+        }                                      \
+    } while (0)
+
+}  // namespace
+
+extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, uint64_t n_edges, uint32_t n_nodes,
+                                  uint32_t m, uint32_t c, uint64_t seed, uint64_t* d_proc, uint64_t* d_local,
+                                  double* d_global, void* stream) {
+    if (m == 0 || c == 0 || n_nodes == 0 || n_nodes == 0xFFFFFFFFu || !d_proc || !d_local) return REPT_E_INVAL;
+    if (c > m && c % m != 0) return REPT_E_INVAL;
+    if (c > kMaxProcessors) return REPT_E_INVAL;
+    if (n_edges > 0 && (!d_src || !d_dst)) return REPT_E_INVAL;
+    if (n_edges >= 0xFFFFFFFFull) return REPT_E_SCRATCH;
+    const Layout L = layout_for(n_nodes, n_edges);
+    if (L.end > REPT_NOALLOC_SCRATCH_BYTES) return REPT_E_SCRATCH;
+    void* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* sc = static_cast<unsigned char*>(base);
+
+    StreamDev d{};
+    d.m = m;
+    d.c = c;
+    d.groups = c <= m ? 1u : c / m;
+    d.n_nodes = n_nodes;
+    d.seed = seed;
+    d.meta = reinterpret_cast<uint2*>(sc + L.meta);
+    d.add = reinterpret_cast<uint32_t*>(sc + L.add);
+    d.touched = reinterpret_cast<uint32_t*>(sc + L.touched);
+    d.grow_rel = reinterpret_cast<uint32_t*>(sc + L.grow_rel);
+    d.bins = reinterpret_cast<uint32_t*>(sc + L.bins);
+    d.bin_cap = n_edges ? n_edges : 1;
+    d.ctrl = reinterpret_cast<Ctrl*>(sc + L.ctrl);
+    d.pool = reinterpret_cast<uint2*>(sc + L.pool);
+    d.pool_quads = L.pool_quads;
+    d.local = reinterpret_cast<unsigned long long*>(d_local);
+    d.proc = reinterpret_cast<unsigned long long*>(d_proc);
+
+    // the scratch keeps the previous call's contents: clear what must start empty
+    NA_CUDA(cudaMemsetAsync(d.meta, 0, (size_t)n_nodes * sizeof(uint2), st));
+    NA_CUDA(cudaMemsetAsync(d.add, 0, (size_t)n_nodes * sizeof(uint32_t), st));
+    NA_CUDA(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), st));
+    NA_CUDA(cudaMemsetAsync(d.pool, 0xFF, L.pool_quads * 32ull, st));
+    NA_CUDA(cudaMemsetAsync(d_proc, 0, (size_t)c * sizeof(uint64_t), st));
+    NA_CUDA(cudaMemsetAsync(d_local, 0, (size_t)n_nodes * sizeof(uint64_t), st));
+
+    if (n_edges > 0) {
+        int dev = 0, sms = 0;
+        NA_CUDA(cudaGetDevice(&dev));
+        NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const BatchDev b{d_src, d_dst, n_edges, 0ull};
+        const int threads = 256;
+        const unsigned long long blocks = (n_edges + threads - 1) / threads;
+        const int grid = (int)(blocks < (unsigned long long)sms * 8 ? blocks : (unsigned long long)sms * 8);
+        k_classify<<<grid, threads, 0, st>>>(d, b);
+        k_plan<<<grid, threads, 0, st>>>(d);
+        k_commit<<<grid, threads, 0, st>>>(d);
+        k_insert<<<grid, threads, 0, st>>>(d, b);
+        const unsigned long long want_i = (n_edges * 8 + 255) / 256;
+        const int grid_i = (int)(want_i < (unsigned long long)sms * 4 ? want_i : (unsigned long long)sms * 4);
+        k_intersect<false><<<grid_i, 256, c * sizeof(unsigned long long), st>>>(d, b);
+        NA_CUDA(cudaPeekAtLastError());
+    }
+    if (d_global) {
+        const double md = (double)m;
+        const double f = c <= m ? md * md / (double)c : md / (double)(c / m);
+        k_global_estimate<<<1, 256, 0, st>>>(d.proc, c, f, d_global);
+        NA_CUDA(cudaPeekAtLastError());
+    }
+    unsigned int status = 0;
+    NA_CUDA(cudaMemcpyAsync(&status, &d.ctrl->status, sizeof(status), cudaMemcpyDeviceToHost, st));
+    NA_CUDA(cudaStreamSynchronize(st));
+    if (status & kStRange) return REPT_E_RANGE;
+    if (status & kStCapacity) return REPT_E_INTERNAL;  // impossible: the pool is sized for the worst case
+    if (status & kStInternal) return REPT_E_INTERNAL;
+    return REPT_OK;
+}
