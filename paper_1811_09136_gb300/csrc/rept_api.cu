@@ -271,6 +271,7 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     d.groups = s->groups;
     d.n_nodes = n;
     d.seed = cfg->seed;
+    d.fm = make_fastmod(cfg->m);
     const unsigned long long mb = cfg->max_batch ? cfg->max_batch : (1ull << 20);
     unsigned long long quads = cfg->expected_edges ? quads_bound(cfg->expected_edges) : quads_bound(mb);
     if (quads > 0xFFFFFFFFull) quads = 0xFFFFFFFFull;

@@ -38,6 +38,46 @@ __host__ __device__ __forceinline__ int bin_of(uint32_t lg_s) { return lg_s <= 5
 // status bits (sticky)
 constexpr unsigned kStRange = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeout = 8u;
 
+// x mod m for 64-bit x and 32-bit m >= 2 without a division: Lemire, Kaser, Kurz, "Faster Remainder
+// by Direct Computation" (2019).  With the 128-bit magic M = floor((2^128 - 1) / m) + 1, the low 128
+// bits of M * x, multiplied by m, hold x mod m in their top 64 bits; 128 >= 64 + log2(m) bits of magic
+// make this exact for every 64-bit x.
+struct FastMod {
+    uint64_t mh, ml;  // M = mh * 2^64 + ml
+    uint32_t m;
+};
+
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+inline FastMod make_fastmod(uint32_t m) {
+    FastMod f{0, 0, m};
+    if (m >= 2) {
+        // floor((2^128 - 1) / m) + 1, by long division of the all-ones 128-bit value
+        const uint64_t ones = ~0ull;
+        const uint64_t qh = ones / m, rh = ones % m;
+        const unsigned __int128 low = ((unsigned __int128)rh << 64) | ones;
+        const uint64_t ql = (uint64_t)(low / m);
+        f.ml = ql + 1;
+        f.mh = qh + (f.ml == 0 ? 1 : 0);
+    }
+    return f;
+}
+
+__host__ __device__ __forceinline__ uint32_t fast_mod(uint64_t x, const FastMod& f) {
+    if (f.m < 2) return 0u;
+    const uint64_t ll = f.ml * x;                        // low 128 bits of M * x: (lh, ll)
+    const uint64_t lh = mulhi64(f.ml, x) + f.mh * x;
+    const uint64_t a = lh * (uint64_t)f.m;               // (lh, ll) * m >> 128
+    const uint64_t b = mulhi64(ll, (uint64_t)f.m);
+    return (uint32_t)(mulhi64(lh, (uint64_t)f.m) + ((a + b) < a ? 1u : 0u));
+}
+
 struct Ctrl {
     unsigned long long n_touched;   // nodes in touched[] this batch
     unsigned long long need_quads;  // table space requested by this batch, in 4-slot units
@@ -57,6 +97,7 @@ struct Ctrl {
 struct StreamDev {
     uint32_t m, c, groups, n_nodes;
     uint64_t seed;
+    FastMod fm;  // x mod m
     uint2* meta;
     uint2* pool;
     unsigned long long pool_quads;
@@ -87,9 +128,9 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 
 // h_k({a, b}) given the group seed s_k.
-__device__ __forceinline__ uint32_t colour_of(uint32_t a, uint32_t b, uint64_t s_k, uint32_t m) {
+__device__ __forceinline__ uint32_t colour_of(uint32_t a, uint32_t b, uint64_t s_k, const FastMod& fm) {
     uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
-    return (uint32_t)(splitmix64(((lo << 32) | hi) ^ s_k) % (uint64_t)m);
+    return fast_mod(splitmix64(((lo << 32) | hi) ^ s_k), fm);
 }
 
 __device__ __forceinline__ uint64_t group_seed(uint64_t seed, uint32_t k) { return seed + (uint64_t)k * kGoldenGamma; }
@@ -97,7 +138,7 @@ __device__ __forceinline__ uint64_t group_seed(uint64_t seed, uint32_t k) { retu
 // Is edge {u, v} kept by some processor (k*m + h_k(u,v) < c for some group k)?
 __device__ __forceinline__ bool kept_by_any(const StreamDev& d, uint32_t u, uint32_t v) {
     for (uint32_t k = 0; k < d.groups; ++k) {
-        uint32_t j = colour_of(u, v, group_seed(d.seed, k), d.m);
+        uint32_t j = colour_of(u, v, group_seed(d.seed, k), d.fm);
         if (k * d.m + j < d.c) return true;
     }
     return false;
@@ -115,8 +156,11 @@ __host__ __device__ __forceinline__ uint32_t table_lg(uint32_t cnt) {
     return lg < 2u ? 2u : lg;
 }
 
-// Home slot of neighbour w in a table of 2^lg slots (Fibonacci hashing).
-__device__ __forceinline__ uint32_t home_slot(uint32_t w, uint32_t lg) { return (w * 0x9E3779B1u) >> (32u - lg); }
+// Home slot of neighbour w in a table of 2^lg slots: the first slot of a 4-slot (32-byte) bucket
+// chosen by Fibonacci hashing.  Probing is linear from there, so a lookup reads whole sectors.
+__device__ __forceinline__ uint32_t home_slot(uint32_t w, uint32_t lg) {
+    return ((w * 0x9E3779B1u) >> (32u - lg)) & ~3u;
+}
 
 __device__ __forceinline__ unsigned long long pack_slot(uint32_t nbr, uint32_t eidx) {
     return ((unsigned long long)eidx << 32) | nbr;

@@ -171,19 +171,24 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
     }
 }
 
-// Probe the table (2^lg slots at `base`) for neighbour w.  Returns the entry's stream index,
-// or kEmptyId when w is absent; `slots` receives the number of slots read.
+// Look neighbour w up in the table of 2^lg slots at `base` (lg >= 2): read whole 4-slot buckets
+// from w's home bucket on until w or an empty slot shows up.  Returns w's stream index, or kEmptyId
+// when w is absent; `slots` receives the number of slots read.
 __device__ __forceinline__ uint32_t table_find(const uint2* __restrict__ pool, unsigned long long base, uint32_t lg,
                                                uint32_t w, uint32_t& slots) {
     const uint32_t mask = (1u << lg) - 1u;
     uint32_t h = home_slot(w, lg);
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const uint2 s = pool[base + h];
-        if (s.x == w) { slots = probe + 1u; return s.y; }
-        if (s.x == kEmptyId) { slots = probe + 1u; return kEmptyId; }
-        h = (h + 1u) & mask;
+    const uint4* tab = reinterpret_cast<const uint4*>(pool + base);
+    for (uint32_t probe = 0; probe <= mask; probe += 4u) {
+        const uint4 p0 = tab[h >> 1], p1 = tab[(h >> 1) + 1];
+        slots = probe + 4u;
+        if (p0.x == w) return p0.y;
+        if (p0.z == w) return p0.w;
+        if (p1.x == w) return p1.y;
+        if (p1.z == w) return p1.w;
+        if (p0.x == kEmptyId || p0.z == kEmptyId || p1.x == kEmptyId || p1.z == kEmptyId) return kEmptyId;
+        h = (h + 4u) & mask;
     }
-    slots = mask + 1u;
     return kEmptyId;
 }
 
@@ -199,8 +204,8 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
     uint32_t found = 0;
     for (uint32_t k = 0; k < d.groups; ++k) {
         const uint64_t sk = group_seed(d.seed, k);
-        const uint32_t js = colour_of(s, w, sk, d.m);
-        if (k * d.m + js < d.c && colour_of(l, w, sk, d.m) == js) {
+        const uint32_t js = colour_of(s, w, sk, d.fm);
+        if (k * d.m + js < d.c && colour_of(l, w, sk, d.fm) == js) {
             ++found;
             atomicAdd(&s_proc[k * d.m + js], 1ull);
         }
@@ -258,39 +263,14 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const BatchDe
     }
 }
 
-// Two probes of the same table interleaved, so that each lane keeps two loads in flight.
-__device__ __forceinline__ void table_find2(const uint2* __restrict__ pool, unsigned long long base, uint32_t lg,
-                                            uint32_t w1, bool a1, uint32_t w2, bool a2, uint32_t& r1, uint32_t& r2,
-                                            uint32_t& slots) {
-    const uint32_t mask = (1u << lg) - 1u;
-    uint32_t h1 = home_slot(w1, lg), h2 = home_slot(w2, lg);
-    bool d1 = !a1, d2 = !a2;
-    r1 = kEmptyId;
-    r2 = kEmptyId;
-    slots = 0;
-    for (uint32_t probe = 0; probe <= mask && !(d1 && d2); ++probe) {
-        uint2 s1 = make_uint2(kEmptyId, kEmptyId), s2 = s1;
-        if (!d1) s1 = pool[base + h1];
-        if (!d2) s2 = pool[base + h2];
-        if (!d1) {
-            ++slots;
-            if (s1.x == w1) { r1 = s1.y; d1 = true; }
-            else if (s1.x == kEmptyId) d1 = true;
-            else h1 = (h1 + 1u) & mask;
-        }
-        if (!d2) {
-            ++slots;
-            if (s2.x == w2) { r2 = s2.y; d2 = true; }
-            else if (s2.x == kEmptyId) d2 = true;
-            else h2 = (h2 + 1u) & mask;
-        }
-    }
-}
+// Edges whose smaller table has >= 64 slots: a warp per edge.  Each pass reads 128 slots of the
+// smaller table (two 16-byte loads per lane), packs the entries older than the edge into the warp's
+// shared-memory queue, and then probes them with all 32 lanes.
+constexpr int kQueue = 128;
 
-// Edges whose smaller table has >= 64 slots: a warp per edge, two slots per lane per 16-byte load.
 template <bool WORK>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const BatchDev& b, uint32_t e,
-                                               unsigned long long* s_proc, Work& wk) {
+                                               unsigned long long* s_proc, uint32_t* queue, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const EdgeView x = edge_view(d, b, e);
     const uint32_t cap_s = 1u << table_lg(x.ms.y), lg_l = table_lg(x.ml.y);
@@ -298,26 +278,36 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const BatchDe
     if (WORK && lane == 0) { wk.entries += x.ms.y; wk.slots += cap_s; }
     const uint4* tab = reinterpret_cast<const uint4*>(d.pool + base_s);  // 32-byte aligned table
     uint32_t total = 0;
-    for (uint32_t j0 = 0; j0 < cap_s; j0 += 64u) {
-        const uint4 q = tab[(j0 >> 1) + lane];
-        const bool a1 = q.x != kEmptyId && q.y < x.t, a2 = q.z != kEmptyId && q.w < x.t;
+    for (uint32_t j0 = 0; j0 < cap_s; j0 += 128u) {
+        uint32_t n_q = 0;
+#pragma unroll
+        for (uint32_t half = 0; half < 2; ++half) {
+            const uint32_t jj = j0 + 64u * half;  // cap_s is a multiple of 64
+            uint4 q = make_uint4(kEmptyId, 0u, kEmptyId, 0u);
+            if (jj < cap_s) q = tab[(jj >> 1) + lane];
+            const bool a1 = q.x != kEmptyId && q.y < x.t, a2 = q.z != kEmptyId && q.w < x.t;
+            const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
+            const unsigned below = (1u << lane) - 1u;
+            if (a1) queue[n_q + __popc(m1 & below)] = q.x;
+            n_q += __popc(m1);
+            if (a2) queue[n_q + __popc(m2 & below)] = q.z;
+            n_q += __popc(m2);
+        }
+        __syncwarp();
         uint32_t found = 0;
-        if (a1 || a2) {
-            uint32_t r1, r2, nslots;
-            table_find2(d.pool, base_l, lg_l, q.x, a1, q.z, a2, r1, r2, nslots);
-            if (WORK) { wk.probes += (uint32_t)a1 + (uint32_t)a2; wk.pslots += nslots; }
-            if (r1 < x.t) {
-                const uint32_t f = count_wedge(d, x.s, x.l, q.x, s_proc);
-                found += f;
-                if (WORK) { ++wk.wedges; wk.counted += f; }
-            }
-            if (r2 < x.t) {
-                const uint32_t f = count_wedge(d, x.s, x.l, q.z, s_proc);
+        for (uint32_t k = lane; k < n_q; k += 32u) {
+            const uint32_t w = queue[k];
+            uint32_t nslots = 0;
+            const uint32_t tl = table_find(d.pool, base_l, lg_l, w, nslots);
+            if (WORK) { ++wk.probes; wk.pslots += nslots; }
+            if (tl < x.t) {
+                const uint32_t f = count_wedge(d, x.s, x.l, w, s_proc);
                 found += f;
                 if (WORK) { ++wk.wedges; wk.counted += f; }
             }
         }
         total += __reduce_add_sync(0xFFFFFFFFu, found);
+        __syncwarp();
     }
     if (lane == 0 && total) {
         atomicAdd(&d.local[x.u], (unsigned long long)total);
@@ -348,7 +338,7 @@ __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, const BatchDe
 
 template <bool WORK>
 __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, const BatchDev& b, int cls,
-                                               unsigned long long* s_proc, Work& wk) {
+                                               unsigned long long* s_proc, uint32_t* queue, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long count = d.ctrl->bin_count[cls];
     const uint32_t* items = d.bins + (unsigned long long)cls * d.bin_cap;
@@ -357,7 +347,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, const BatchDe
         if (lane == 0) i = atomicAdd(&d.ctrl->bin_next[cls], 1ull);
         i = __shfl_sync(0xFFFFFFFFu, i, 0);
         if (i >= count) break;
-        intersect_warp<WORK>(d, b, items[i], s_proc, wk);
+        intersect_warp<WORK>(d, b, items[i], s_proc, queue, wk);
     }
 }
 
@@ -365,15 +355,17 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, const BatchDe
 // k_insert; warps claim work dynamically, largest class first.  Dynamic shared memory: c uint64
 // counters (tau^(i) of this block).  WORK = true also tallies the table reads.
 template <bool WORK>
-__global__ void __launch_bounds__(256) k_intersect(StreamDev d, BatchDev b) {
+__global__ void __launch_bounds__(256, 4) k_intersect(StreamDev d, BatchDev b) {
     extern __shared__ unsigned long long s_proc[];
+    __shared__ uint32_t s_queue[256 / 32][kQueue];
     for (uint32_t i = threadIdx.x; i < d.c; i += blockDim.x) s_proc[i] = 0ull;
     __syncthreads();
     const unsigned lane = threadIdx.x & 31u;
+    uint32_t* queue = s_queue[threadIdx.x >> 5];
     Work wk;
     if (d.ctrl->status == 0u) {
-        drain_warp_bin<WORK>(d, b, 5, s_proc, wk);
-        drain_warp_bin<WORK>(d, b, 4, s_proc, wk);
+        drain_warp_bin<WORK>(d, b, 5, s_proc, queue, wk);
+        drain_warp_bin<WORK>(d, b, 4, s_proc, queue, wk);
         drain_tile_bin<32, WORK>(d, b, 3, s_proc, wk);
         drain_tile_bin<16, WORK>(d, b, 2, s_proc, wk);
         drain_tile_bin<8, WORK>(d, b, 1, s_proc, wk);
