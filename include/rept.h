@@ -70,7 +70,8 @@ extern "C" {
 #define REPT_K_INSERT 3
 #define REPT_K_INTERSECT 4
 #define REPT_K_ESTIMATE 5
-#define REPT_NUM_KERNELS 6
+#define REPT_K_SORT 6
+#define REPT_NUM_KERNELS 7
 
 typedef struct rept_config {
     uint32_t m;              /* 1/p; m >= 1 (the paper takes m >= 2; m = 1 keeps every edge) */
@@ -192,7 +193,7 @@ void rept_destroy(rept_state* s);
  * control block) lives in one statically allocated device array of
  * REPT_NOALLOC_SCRATCH_BYTES (64 MiB) inside this library; every GPU that
  * loads the library holds that array until the process exits.  A problem
- * needs 12 * n_nodes + 104 * n_edges + 8 KiB bytes of it (for example
+ * needs 12 * n_nodes + 94 * n_edges + 200 KiB bytes of it (for example
  * 2^20 nodes and 500,000 edges); larger problems return REPT_E_SCRATCH
  * before any device work is enqueued.  c must be at most 4096.
  *

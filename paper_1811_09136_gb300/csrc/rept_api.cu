@@ -128,16 +128,18 @@ int ensure_batch_scratch(rept_state* s, unsigned long long n, cudaStream_t st) {
     const unsigned long long old = s->max_batch;
     dev_free(s, s->d.touched, 2 * old * sizeof(uint32_t));
     dev_free(s, s->d.grow_rel, 2 * old * sizeof(uint32_t));
-    dev_free(s, s->d.bins, kBins * old * sizeof(uint32_t));
-    s->d.touched = nullptr;
-    s->d.grow_rel = nullptr;
-    s->d.bins = nullptr;
+    dev_free(s, s->d.big, 2 * old * sizeof(uint32_t));
+    dev_free(s, s->d.items, old * sizeof(uint32_t));
+    dev_free(s, s->d.ekey, old * sizeof(uint16_t));
+    s->d.touched = s->d.grow_rel = s->d.big = s->d.items = nullptr;
+    s->d.ekey = nullptr;
     int rc = dev_alloc(s, (void**)&s->d.touched, 2 * n * sizeof(uint32_t));
     if (!rc) rc = dev_alloc(s, (void**)&s->d.grow_rel, 2 * n * sizeof(uint32_t));
-    if (!rc) rc = dev_alloc(s, (void**)&s->d.bins, kBins * n * sizeof(uint32_t));
+    if (!rc) rc = dev_alloc(s, (void**)&s->d.big, 2 * n * sizeof(uint32_t));
+    if (!rc) rc = dev_alloc(s, (void**)&s->d.items, n * sizeof(uint32_t));
+    if (!rc) rc = dev_alloc(s, (void**)&s->d.ekey, n * sizeof(uint16_t));
     if (rc) return rc;
     s->max_batch = n;
-    s->d.bin_cap = n;
     return REPT_OK;
 }
 
@@ -154,7 +156,7 @@ cudaEvent_t take_event(rept_state* s) {
 
 // Launch `fn` on `st`; with REPT_FLAG_PROFILE bracket it with events on the same stream.
 template <class F>
-int timed_launch(rept_state* s, int kernel, cudaStream_t st, F&& fn) {
+int timed_launch(rept_state* s, int kernel, cudaStream_t st, F&& fn, int kernels_in_fn = 1) {
     const bool prof = (s->cfg.flags & REPT_FLAG_PROFILE) != 0;
     cudaEvent_t a = nullptr, b = nullptr;
     if (prof) {
@@ -164,8 +166,8 @@ int timed_launch(rept_state* s, int kernel, cudaStream_t st, F&& fn) {
         REPT_CUDA(cudaEventRecord(a, st));
     }
     fn();
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    s->kernel_launches[kernel] += 1;
+    g_launches.fetch_add((unsigned long long)kernels_in_fn, std::memory_order_relaxed);
+    s->kernel_launches[kernel] += (unsigned long long)kernels_in_fn;
     if (cudaPeekAtLastError() != cudaSuccess) {
         (void)cudaGetLastError();
         return REPT_E_CUDA;
@@ -208,8 +210,17 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
             if ((rc = grow_pool(s, need + need / 2 + 1024, st))) return rc;
         }
     }
-    if ((rc = timed_launch(s, REPT_K_COMMIT, st, [&] { k_commit<<<grid, threads, 0, st>>>(s->d); }))) return rc;
+    if ((rc = timed_launch(s, REPT_K_COMMIT, st, [&] {
+             k_commit<<<grid, threads, 0, st>>>(s->d);
+             k_rehash_big<<<s->sm_count * 4, threads, 0, st>>>(s->d);
+         }, 2)))
+        return rc;
     if ((rc = timed_launch(s, REPT_K_INSERT, st, [&] { k_insert<<<grid, threads, 0, st>>>(s->d, b); }))) return rc;
+    if ((rc = timed_launch(s, REPT_K_SORT, st, [&] {
+             k_sort_scan<<<1, 1024, 0, st>>>(s->d);
+             k_sort_scatter<<<grid, threads, 0, st>>>(s->d, b);
+         }, 2)))
+        return rc;
     const unsigned long long want_i = (n * 8 + 255) / 256;  // work is claimed dynamically; >= 1 block
     const int grid_i = (int)std::min<unsigned long long>(want_i, (unsigned long long)s->grid_intersect);
     const size_t smem = s->cfg.c * sizeof(unsigned long long);
@@ -280,6 +291,7 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if ((rc = dev_alloc(s, (void**)&d.proc, (size_t)cfg->c * sizeof(unsigned long long)))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&d.add, (size_t)n * sizeof(uint32_t)))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&d.ctrl, sizeof(Ctrl)))) return fail(rc);
+    if ((rc = dev_alloc(s, (void**)&d.hist, kSortBuckets * sizeof(uint32_t)))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&d.pool, quads * 32ull))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&s->d_global, sizeof(double)))) return fail(rc);
     d.pool_quads = quads;
@@ -464,7 +476,10 @@ void rept_destroy(rept_state* s) {
     cudaFree(d.pool);
     cudaFree(d.touched);
     cudaFree(d.grow_rel);
-    cudaFree(d.bins);
+    cudaFree(d.big);
+    cudaFree(d.items);
+    cudaFree(d.ekey);
+    cudaFree(d.hist);
     cudaFree(s->stage_src);
     cudaFree(s->stage_dst);
     cudaFree(s->d_global);

@@ -34,6 +34,12 @@ constexpr uint32_t kMaxProcessors = 4096;  // per-block tau^(i) histogram lives 
 // tiles of 4, 8, 16, 32 lanes (one slot per lane), 64..512 slots and >= 1024 slots by a warp.
 constexpr int kBins = 6;
 __host__ __device__ __forceinline__ int bin_of(uint32_t lg_s) { return lg_s <= 5u ? (int)lg_s - 2 : (lg_s <= 9u ? 4 : 5); }
+// Within a class, work items are ordered by a hash of the larger endpoint (kKeyBits bits), so that
+// the edges probing the same large table run back to back and find it in L2.
+constexpr int kKeyBits = 13;
+constexpr uint32_t kKeyBuckets = 1u << kKeyBits;
+constexpr uint32_t kSortBuckets = kBins * kKeyBuckets;
+constexpr uint16_t kNoKey = 0xFFFFu;
 
 // status bits (sticky)
 constexpr unsigned kStRange = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeout = 8u;
@@ -88,9 +94,11 @@ struct Ctrl {
     unsigned int pad;
     // work counters of k_intersect<true> (see rept_stats)
     unsigned long long small_entries, small_slots, probes, probe_slots, wedges, counted;
-    // per-batch work lists of k_intersect: items appended by k_insert, claimed by k_intersect
+    // per-batch work list of k_intersect: class c occupies items[bin_start[c] .. + bin_count[c])
+    unsigned long long bin_start[kBins];
     unsigned long long bin_count[kBins];
     unsigned long long bin_next[kBins];
+    unsigned long long n_big;  // nodes whose large table k_rehash_big moves
 };
 
 // Everything a kernel needs to know about one stream's state.
@@ -106,8 +114,10 @@ struct StreamDev {
     uint32_t* add;
     uint32_t* touched;
     uint32_t* grow_rel;
-    uint32_t* bins;  // kBins lists of bin_cap edge indices (batch-relative)
-    unsigned long long bin_cap;
+    uint16_t* ekey;     // [max_batch] work-class/sort key of each edge, kNoKey if it closes no wedge
+    uint32_t* hist;     // [kSortBuckets] counts, then cursors, of the counting sort by key
+    uint32_t* items;    // [max_batch] edge indices (batch-relative) sorted by key
+    uint32_t* big;      // [2 * max_batch] touched-list indices of nodes with a large table to move
     Ctrl* ctrl;
 };
 

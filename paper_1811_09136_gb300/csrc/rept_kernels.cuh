@@ -38,10 +38,10 @@ __device__ __forceinline__ bool table_insert(uint2* pool, unsigned long long bas
 }
 
 __global__ void k_classify(StreamDev d, BatchDev b) {
-    if (blockIdx.x == 0 && threadIdx.x < kBins) {  // the previous batch's work lists are consumed
-        d.ctrl->bin_count[threadIdx.x] = 0ull;
-        d.ctrl->bin_next[threadIdx.x] = 0ull;
-    }
+    // the previous batch's work list is consumed: clear the counting-sort histogram
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < kSortBuckets; i += gridDim.x * blockDim.x)
+        d.hist[i] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x < kBins) d.ctrl->bin_next[threadIdx.x] = 0ull;
     if (d.ctrl->status) return;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -86,7 +86,8 @@ __global__ void k_plan(StreamDev d) {
     }
 }
 
-// One warp per touched node.
+// Publish the new entry counts of the touched nodes and move the tables that were re-allocated.
+// One thread per touched node; a table of more than 16 slots is left to k_rehash_big (a warp each).
 __global__ void k_commit(StreamDev d) {
     const unsigned status = d.ctrl->status;
     const unsigned long long n_t = d.ctrl->n_touched;
@@ -94,34 +95,69 @@ __global__ void k_commit(StreamDev d) {
     const bool bad = status != 0u || top + need > d.pool_quads;
     if (status == 0u && bad && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&d.ctrl->status, kStCapacity);
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    for (unsigned long long i = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n_t;
-         i += warps) {
-        const uint32_t x = d.touched[i];
-        if (!bad) {
-            const uint2 m = d.meta[x];
-            const uint32_t cnt_new = m.y + d.add[x];
-            const uint32_t rel = d.grow_rel[i];
-            if (rel != kNoGrow) {
-                const unsigned long long new_off = top + rel;
-                const uint32_t lg_new = table_lg(cnt_new);
-                if (m.y > 0) {
-                    const uint32_t old_cap = 1u << table_lg(m.y);
-                    const unsigned long long old_base = 4ull * m.x;
-                    bool ok = true;
-                    for (uint32_t j = lane; j < old_cap; j += 32u) {
-                        const uint2 s = d.pool[old_base + j];
-                        if (s.x != kEmptyId) ok &= table_insert(d.pool, 4ull * new_off, lg_new, s.x, s.y);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n_t;
+         base += stride) {
+        const unsigned long long i = base + lane;
+        bool defer = false;
+        if (i < n_t) {
+            const uint32_t x = d.touched[i];
+            bool done = true;
+            if (!bad) {
+                const uint2 m = d.meta[x];
+                const uint32_t cnt_new = m.y + d.add[x];
+                const uint32_t rel = d.grow_rel[i];
+                if (rel == kNoGrow) {
+                    d.meta[x].y = cnt_new;
+                } else {
+                    const unsigned long long new_off = top + rel;
+                    const uint32_t lg_old = table_lg(m.y);
+                    if (lg_old > 4u) {
+                        defer = true;
+                        done = false;
+                    } else {
+                        bool ok = true;
+                        const uint32_t lg_new = table_lg(cnt_new);
+                        for (uint32_t j = 0; m.y > 0u && j < (1u << lg_old); ++j) {
+                            const uint2 sl = d.pool[4ull * m.x + j];
+                            if (sl.x != kEmptyId) ok &= table_insert(d.pool, 4ull * new_off, lg_new, sl.x, sl.y);
+                        }
+                        if (!ok) atomicOr(&d.ctrl->status, kStInternal);
+                        d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
                     }
-                    if (!ok) atomicOr(&d.ctrl->status, kStInternal);
                 }
-                __syncwarp();
-                if (lane == 0) d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
-            } else if (lane == 0) {
-                d.meta[x].y = cnt_new;
             }
+            if (done) d.add[x] = 0u;
         }
-        if (lane == 0) d.add[x] = 0u;
+        const unsigned long long o = warp_reserve(&d.ctrl->n_big, defer ? 1ull : 0ull);
+        if (defer) d.big[o] = (uint32_t)i;
+    }
+}
+
+// Move the large tables listed by k_commit: one warp per node.
+__global__ void k_rehash_big(StreamDev d) {
+    const unsigned long long n_big = d.ctrl->n_big, top = d.ctrl->pool_top;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long k = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_big;
+         k += warps) {
+        const uint32_t i = d.big[k];
+        const uint32_t x = d.touched[i];
+        const uint2 m = d.meta[x];
+        const uint32_t cnt_new = m.y + d.add[x];
+        const unsigned long long new_off = top + d.grow_rel[i];
+        const uint32_t lg_new = table_lg(cnt_new), old_cap = 1u << table_lg(m.y);
+        bool ok = true;
+        for (uint32_t j = lane; j < old_cap; j += 32u) {
+            const uint2 sl = d.pool[4ull * m.x + j];
+            if (sl.x != kEmptyId) ok &= table_insert(d.pool, 4ull * new_off, lg_new, sl.x, sl.y);
+        }
+        if (!ok) atomicOr(&d.ctrl->status, kStInternal);
+        __syncwarp();
+        if (lane == 0) {
+            d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
+            d.add[x] = 0u;
+        }
     }
 }
 
@@ -133,6 +169,7 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
         if (status == 0u) ct->pool_top += ct->need_quads;
         ct->need_quads = 0;
         ct->n_touched = 0;
+        ct->n_big = 0;
     }
     if (status) return;
     const unsigned lane = threadIdx.x & 31u;
@@ -145,7 +182,7 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
         if (valid) { u = b.src[e]; v = b.dst[e]; }
         const bool loop = valid && u == v;
         const bool kept = valid && u != v && kept_by_any(d, u, v);
-        int cls = -1;
+        uint32_t key = kNoKey;
         if (valid && u != v) {
             const uint2 mu = d.meta[u], mv = d.meta[v];
             if (kept) {
@@ -155,19 +192,89 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
                 if (!ok) atomicOr(&ct->status, kStInternal);
             }
             // an edge can close wedges only if both endpoints have stored edges
-            if (mu.y != 0u && mv.y != 0u) cls = bin_of(table_lg(mu.y <= mv.y ? mu.y : mv.y));
+            if (mu.y != 0u && mv.y != 0u) {
+                const bool u_small = mu.y <= mv.y;
+                const uint32_t l = u_small ? v : u;
+                key = (uint32_t)bin_of(table_lg(u_small ? mu.y : mv.y)) * kKeyBuckets +
+                      ((l * 0x9E3779B1u) >> (32 - kKeyBits));
+            }
         }
-        for (int k = 0; k < kBins; ++k) {
-            const unsigned mask = __ballot_sync(0xFFFFFFFFu, cls == k);
-            if (mask == 0u) continue;
-            const int leader = __ffs(mask) - 1;
-            unsigned long long pos = 0;
-            if ((int)lane == leader) pos = atomicAdd(&ct->bin_count[k], (unsigned long long)__popc(mask));
-            pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-            if (cls == k) d.bins[k * d.bin_cap + pos + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)e;
+        if (valid) d.ekey[e] = (uint16_t)key;
+        {
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+            if (key != kNoKey && lane == (unsigned)(__ffs(peers) - 1))
+                atomicAdd(&d.hist[key], (uint32_t)__popc(peers));
         }
         warp_reserve(&ct->self_loops, loop ? 1ull : 0ull);
         warp_reserve(&ct->stored, kept ? 1ull : 0ull);
+    }
+}
+
+// Exclusive scan of the counting-sort histogram (one block of 1024 threads): counts become the
+// first position of each key, and the class boundaries are recorded.
+__global__ void __launch_bounds__(1024) k_sort_scan(StreamDev d) {
+    constexpr uint32_t kPer = kSortBuckets / 1024;
+    __shared__ uint32_t warp_sum[32];
+    if (d.ctrl->status) return;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
+    uint32_t local[kPer];
+    uint32_t sum = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        local[k] = d.hist[tid * kPer + k];
+        sum += local[k];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = warp_sum[lane], wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= (uint32_t)o) wi += y;
+        }
+        warp_sum[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t run = warp_sum[wid] + incl - sum;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        const uint32_t key = tid * kPer + k;
+        if (key % kKeyBuckets == 0u) d.ctrl->bin_start[key / kKeyBuckets] = run;
+        d.hist[key] = run;
+        run += local[k];
+    }
+    __syncthreads();
+    if (tid == 1023) {  // totals: the last thread's running sum is the number of items
+        unsigned long long prev = run;
+        for (int c = kBins - 1; c >= 0; --c) {
+            d.ctrl->bin_count[c] = prev - d.ctrl->bin_start[c];
+            prev = d.ctrl->bin_start[c];
+        }
+    }
+}
+
+// Scatter each edge that can close a wedge to its place in the sorted work list.
+__global__ void k_sort_scatter(StreamDev d, BatchDev b) {
+    if (d.ctrl->status) return;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < b.n;
+         base += stride) {
+        const unsigned long long e = base + lane;
+        const uint32_t key = e < b.n ? (uint32_t)d.ekey[e] : (uint32_t)kNoKey;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+        const int leader = __ffs(peers) - 1;
+        uint32_t pos = 0;
+        if (key != kNoKey && (int)lane == leader) pos = atomicAdd(&d.hist[key], (uint32_t)__popc(peers));
+        pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+        if (key != kNoKey) d.items[pos + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)e;
     }
 }
 
@@ -321,7 +428,7 @@ __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, const BatchDe
     constexpr uint32_t kPerWarp = 32 / TILE, kRounds = 4, kGrab = kPerWarp * kRounds;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long count = d.ctrl->bin_count[cls];
-    const uint32_t* items = d.bins + (unsigned long long)cls * d.bin_cap;
+    const uint32_t* items = d.items + d.ctrl->bin_start[cls];
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&d.ctrl->bin_next[cls], (unsigned long long)kGrab);
@@ -341,7 +448,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, const BatchDe
                                                unsigned long long* s_proc, uint32_t* queue, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long count = d.ctrl->bin_count[cls];
-    const uint32_t* items = d.bins + (unsigned long long)cls * d.bin_cap;
+    const uint32_t* items = d.items + d.ctrl->bin_start[cls];
     for (;;) {
         unsigned long long i = 0;
         if (lane == 0) i = atomicAdd(&d.ctrl->bin_next[cls], 1ull);

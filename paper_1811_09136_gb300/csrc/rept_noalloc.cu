@@ -25,7 +25,7 @@ inline unsigned long long align256(unsigned long long x) { return (x + 255ull) &
 
 // Offsets of the state inside the scratch area for n nodes and E edges.
 struct Layout {
-    unsigned long long meta, add, touched, grow_rel, bins, ctrl, pool, end;
+    unsigned long long meta, add, touched, grow_rel, big, items, ekey, hist, ctrl, pool, end;
     unsigned long long pool_quads;
 };
 
@@ -36,7 +36,10 @@ Layout layout_for(unsigned long long n, unsigned long long E) {
     L.add = o;      o = align256(o + n * sizeof(uint32_t));
     L.touched = o;  o = align256(o + 2 * E * sizeof(uint32_t));
     L.grow_rel = o; o = align256(o + 2 * E * sizeof(uint32_t));
-    L.bins = o;     o = align256(o + (unsigned long long)kBins * E * sizeof(uint32_t));
+    L.big = o;      o = align256(o + 2 * E * sizeof(uint32_t));
+    L.items = o;    o = align256(o + E * sizeof(uint32_t));
+    L.ekey = o;     o = align256(o + E * sizeof(uint16_t));
+    L.hist = o;     o = align256(o + kSortBuckets * sizeof(uint32_t));
     L.ctrl = o;     o = align256(o + sizeof(Ctrl));
     // From an empty state every node's table is allocated once, with at most 4 slots per entry:
     // at most 8 slots (2 quads) per edge.
@@ -99,8 +102,10 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
     d.add = reinterpret_cast<uint32_t*>(sc + L.add);
     d.touched = reinterpret_cast<uint32_t*>(sc + L.touched);
     d.grow_rel = reinterpret_cast<uint32_t*>(sc + L.grow_rel);
-    d.bins = reinterpret_cast<uint32_t*>(sc + L.bins);
-    d.bin_cap = n_edges ? n_edges : 1;
+    d.big = reinterpret_cast<uint32_t*>(sc + L.big);
+    d.items = reinterpret_cast<uint32_t*>(sc + L.items);
+    d.ekey = reinterpret_cast<uint16_t*>(sc + L.ekey);
+    d.hist = reinterpret_cast<uint32_t*>(sc + L.hist);
     d.ctrl = reinterpret_cast<Ctrl*>(sc + L.ctrl);
     d.pool = reinterpret_cast<uint2*>(sc + L.pool);
     d.pool_quads = L.pool_quads;
@@ -126,7 +131,10 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
         k_classify<<<grid, threads, 0, st>>>(d, b);
         k_plan<<<grid, threads, 0, st>>>(d);
         k_commit<<<grid, threads, 0, st>>>(d);
+        k_rehash_big<<<sms * 4, threads, 0, st>>>(d);
         k_insert<<<grid, threads, 0, st>>>(d, b);
+        k_sort_scan<<<1, 1024, 0, st>>>(d);
+        k_sort_scatter<<<grid, threads, 0, st>>>(d, b);
         const unsigned long long want_i = (n_edges * 8 + 255) / 256;
         const int grid_i = (int)(want_i < (unsigned long long)sms * 4 ? want_i : (unsigned long long)sms * 4);
         k_intersect<false><<<grid_i, 256, c * sizeof(unsigned long long), st>>>(d, b);

@@ -22,7 +22,7 @@ FLAG_FIXED_POOL = 1
 FLAG_SYNC = 2
 FLAG_PROFILE = 4
 FLAG_WORK_COUNTERS = 8
-KERNELS = ("classify", "plan", "commit", "insert", "intersect", "estimate")
+KERNELS = ("classify", "plan", "commit", "insert", "intersect", "estimate", "sort")
 
 
 class ReptError(RuntimeError):
