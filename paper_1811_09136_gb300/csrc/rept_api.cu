@@ -140,6 +140,7 @@ int ensure_batch_scratch(rept_state* s, unsigned long long n, cudaStream_t st) {
     if (!rc) rc = dev_alloc(s, (void**)&s->d.ekey, n * sizeof(uint16_t));
     if (rc) return rc;
     s->max_batch = n;
+    s->d.big_cap = 2 * n;
     return REPT_OK;
 }
 
@@ -213,7 +214,8 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
     if ((rc = timed_launch(s, REPT_K_COMMIT, st, [&] {
              k_commit<<<grid, threads, 0, st>>>(s->d);
              k_rehash_big<<<s->sm_count * 4, threads, 0, st>>>(s->d);
-         }, 2)))
+             k_rehash_huge<<<s->sm_count * 2, 1024, 0, st>>>(s->d);
+         }, 3)))
         return rc;
     if ((rc = timed_launch(s, REPT_K_INSERT, st, [&] { k_insert<<<grid, threads, 0, st>>>(s->d, b); }))) return rc;
     if ((rc = timed_launch(s, REPT_K_SORT, st, [&] {

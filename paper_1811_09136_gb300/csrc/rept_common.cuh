@@ -98,7 +98,9 @@ struct Ctrl {
     unsigned long long bin_start[kBins];
     unsigned long long bin_count[kBins];
     unsigned long long bin_next[kBins];
-    unsigned long long n_big;  // nodes whose large table k_rehash_big moves
+    unsigned long long n_big;   // nodes whose table (32..2048 slots) k_rehash_big moves, a warp each
+    unsigned long long n_huge;  // nodes whose table (>= 4096 slots) k_rehash_huge moves, a block each
+    unsigned long long huge_next;
 };
 
 // Everything a kernel needs to know about one stream's state.
@@ -117,7 +119,9 @@ struct StreamDev {
     uint16_t* ekey;     // [max_batch] work-class/sort key of each edge, kNoKey if it closes no wedge
     uint32_t* hist;     // [kSortBuckets] counts, then cursors, of the counting sort by key
     uint32_t* items;    // [max_batch] edge indices (batch-relative) sorted by key
-    uint32_t* big;      // [2 * max_batch] touched-list indices of nodes with a large table to move
+    uint32_t* big;      // [big_cap] touched-list indices of nodes with a large table to move: the
+                        // k_rehash_big list from the front, the k_rehash_huge list from the back
+    unsigned long long big_cap;
     Ctrl* ctrl;
 };
 

@@ -99,7 +99,7 @@ __global__ void k_commit(StreamDev d) {
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n_t;
          base += stride) {
         const unsigned long long i = base + lane;
-        bool defer = false;
+        bool defer = false, huge = false;
         if (i < n_t) {
             const uint32_t x = d.touched[i];
             bool done = true;
@@ -113,7 +113,8 @@ __global__ void k_commit(StreamDev d) {
                     const unsigned long long new_off = top + rel;
                     const uint32_t lg_old = table_lg(m.y);
                     if (lg_old > 4u) {
-                        defer = true;
+                        defer = lg_old <= 11u;
+                        huge = !defer;
                         done = false;
                     } else {
                         bool ok = true;
@@ -131,6 +132,8 @@ __global__ void k_commit(StreamDev d) {
         }
         const unsigned long long o = warp_reserve(&d.ctrl->n_big, defer ? 1ull : 0ull);
         if (defer) d.big[o] = (uint32_t)i;
+        const unsigned long long h = warp_reserve(&d.ctrl->n_huge, huge ? 1ull : 0ull);
+        if (huge) d.big[d.big_cap - 1 - h] = (uint32_t)i;
     }
 }
 
@@ -161,6 +164,41 @@ __global__ void k_rehash_big(StreamDev d) {
     }
 }
 
+// Move the tables of >= 4096 slots listed by k_commit: blocks claim one node at a time.
+__global__ void __launch_bounds__(1024) k_rehash_huge(StreamDev d) {
+    __shared__ unsigned long long s_k;
+    __shared__ int s_bad;
+    const unsigned long long n_huge = d.ctrl->n_huge, top = d.ctrl->pool_top;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_k = atomicAdd(&d.ctrl->huge_next, 1ull);
+            s_bad = 0;
+        }
+        __syncthreads();
+        const unsigned long long k = s_k;
+        if (k >= n_huge) break;
+        const uint32_t i = d.big[d.big_cap - 1 - k];
+        const uint32_t x = d.touched[i];
+        const uint2 m = d.meta[x];
+        const uint32_t cnt_new = m.y + d.add[x];
+        const unsigned long long new_off = top + d.grow_rel[i];
+        const uint32_t lg_new = table_lg(cnt_new), old_cap = 1u << table_lg(m.y);
+        bool ok = true;
+        for (uint32_t j = threadIdx.x; j < old_cap; j += blockDim.x) {
+            const uint2 sl = d.pool[4ull * m.x + j];
+            if (sl.x != kEmptyId) ok &= table_insert(d.pool, 4ull * new_off, lg_new, sl.x, sl.y);
+        }
+        if (!ok) s_bad = 1;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_bad) atomicOr(&d.ctrl->status, kStInternal);
+            d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
+            d.add[x] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_insert(StreamDev d, BatchDev b) {
     Ctrl* ct = d.ctrl;
     const unsigned status = ct->status;
@@ -170,6 +208,8 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
         ct->need_quads = 0;
         ct->n_touched = 0;
         ct->n_big = 0;
+        ct->n_huge = 0;
+        ct->huge_next = 0;
     }
     if (status) return;
     const unsigned lane = threadIdx.x & 31u;
@@ -305,7 +345,8 @@ struct Work {
 };
 
 // Wedge (s, w), (l, w), both edges older than the arriving edge (s, l): count it for every hash group
-// whose colour of the two edges agrees and names a kept processor.  Returns the number of groups.
+// whose colour of the two edges agrees and names a kept processor, and add the number of such groups
+// to tau_s, tau_l and tau_w (Algorithm 1's local updates, one wedge at a time).
 __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, uint32_t l, uint32_t w,
                                                 unsigned long long* s_proc) {
     uint32_t found = 0;
@@ -317,11 +358,55 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
             atomicAdd(&s_proc[k * d.m + js], 1ull);
         }
     }
-    if (found) atomicAdd(&d.local[w], (unsigned long long)found);
+    if (found) {
+        atomicAdd(&d.local[w], (unsigned long long)found);
+        atomicAdd(&d.local[s], (unsigned long long)found);
+        atomicAdd(&d.local[l], (unsigned long long)found);
+    }
     return found;
 }
 
-// The endpoints of edge e in the order (smaller table, larger table); false if either table is empty.
+// Per-warp queue of closed wedges (s, l, w) in shared memory.  Wedges are pushed as the probes find
+// them and coloured 32 at a time, so that the hash work runs on full warps.  `n` is warp-uniform.
+constexpr int kMatchQ = 64;
+struct MatchQueue {
+    uint32_t* s;
+    uint32_t* l;
+    uint32_t* w;
+    uint32_t n;
+};
+
+template <bool WORK>
+__device__ __forceinline__ void mq_flush(const StreamDev& d, MatchQueue& q, uint32_t take,
+                                         unsigned long long* s_proc, Work& wk) {
+    const unsigned lane = threadIdx.x & 31u;
+    if (lane < take) {
+        const uint32_t i = q.n - take + lane;
+        const uint32_t f = count_wedge(d, q.s[i], q.l[i], q.w[i], s_proc);
+        if (WORK) wk.counted += f;
+    }
+    q.n -= take;
+    __syncwarp();
+}
+
+template <bool WORK>
+__device__ __forceinline__ void mq_push(const StreamDev& d, MatchQueue& q, bool has, uint32_t s, uint32_t l,
+                                        uint32_t w, unsigned long long* s_proc, Work& wk) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, has);
+    if (has) {
+        const uint32_t i = q.n + __popc(mask & ((1u << lane) - 1u));
+        q.s[i] = s;
+        q.l[i] = l;
+        q.w[i] = w;
+        if (WORK) ++wk.wedges;
+    }
+    q.n += __popc(mask);
+    __syncwarp();
+    if (q.n >= 32u) mq_flush<WORK>(d, q, 32u, s_proc, wk);
+}
+
+// The endpoints of edge e in the order (smaller table, larger table).
 struct EdgeView {
     uint32_t u, v, s, l, t;
     uint2 ms, ml;
@@ -344,9 +429,10 @@ __device__ __forceinline__ EdgeView edge_view(const StreamDev& d, const BatchDev
 // Edges whose smaller table has exactly TILE slots: one tile of TILE lanes per edge, one slot per lane.
 template <int TILE, bool WORK>
 __device__ __forceinline__ void intersect_tile(const StreamDev& d, const BatchDev& b, uint32_t e, bool valid,
-                                               unsigned long long* s_proc, Work& wk) {
+                                               unsigned long long* s_proc, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u, j = lane & (TILE - 1);
-    uint32_t found = 0;
+    bool has = false;
+    uint32_t w = 0;
     EdgeView x{};
     if (valid) {
         x = edge_view(d, b, e);
@@ -356,35 +442,28 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const BatchDe
             uint32_t nslots = 0;
             const uint32_t tl = table_find(d.pool, 4ull * x.ml.x, table_lg(x.ml.y), es.x, nslots);
             if (WORK) { ++wk.probes; wk.pslots += nslots; }
-            if (tl < x.t) {  // kEmptyId (absent) is never < t
-                found = count_wedge(d, x.s, x.l, es.x, s_proc);
-                if (WORK) { ++wk.wedges; wk.counted += found; }
-            }
+            has = tl < x.t;  // kEmptyId (absent) is never < t
+            w = es.x;
         }
     }
-#pragma unroll
-    for (int o = TILE / 2; o > 0; o >>= 1) found += __shfl_xor_sync(0xFFFFFFFFu, found, o);
-    if (valid && j == 0 && found) {
-        atomicAdd(&d.local[x.u], (unsigned long long)found);
-        atomicAdd(&d.local[x.v], (unsigned long long)found);
-    }
+    mq_push<WORK>(d, mq, has, x.s, x.l, w, s_proc, wk);
 }
 
 // Edges whose smaller table has >= 64 slots: a warp per edge.  Each pass reads 128 slots of the
 // smaller table (two 16-byte loads per lane), packs the entries older than the edge into the warp's
-// shared-memory queue, and then probes them with all 32 lanes.
+// shared-memory key queue, and then probes them with all 32 lanes.
 constexpr int kQueue = 128;
 
 template <bool WORK>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const BatchDev& b, uint32_t e,
-                                               unsigned long long* s_proc, uint32_t* queue, Work& wk) {
+                                               unsigned long long* s_proc, uint32_t* queue, MatchQueue& mq,
+                                               Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const EdgeView x = edge_view(d, b, e);
     const uint32_t cap_s = 1u << table_lg(x.ms.y), lg_l = table_lg(x.ml.y);
     const unsigned long long base_s = 4ull * x.ms.x, base_l = 4ull * x.ml.x;
     if (WORK && lane == 0) { wk.entries += x.ms.y; wk.slots += cap_s; }
     const uint4* tab = reinterpret_cast<const uint4*>(d.pool + base_s);  // 32-byte aligned table
-    uint32_t total = 0;
     for (uint32_t j0 = 0; j0 < cap_s; j0 += 128u) {
         uint32_t n_q = 0;
 #pragma unroll
@@ -401,30 +480,25 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const BatchDe
             n_q += __popc(m2);
         }
         __syncwarp();
-        uint32_t found = 0;
-        for (uint32_t k = lane; k < n_q; k += 32u) {
-            const uint32_t w = queue[k];
-            uint32_t nslots = 0;
-            const uint32_t tl = table_find(d.pool, base_l, lg_l, w, nslots);
-            if (WORK) { ++wk.probes; wk.pslots += nslots; }
-            if (tl < x.t) {
-                const uint32_t f = count_wedge(d, x.s, x.l, w, s_proc);
-                found += f;
-                if (WORK) { ++wk.wedges; wk.counted += f; }
+        for (uint32_t k0 = 0; k0 < n_q; k0 += 32u) {
+            bool has = false;
+            uint32_t w = 0;
+            if (k0 + lane < n_q) {
+                w = queue[k0 + lane];
+                uint32_t nslots = 0;
+                const uint32_t tl = table_find(d.pool, base_l, lg_l, w, nslots);
+                if (WORK) { ++wk.probes; wk.pslots += nslots; }
+                has = tl < x.t;
             }
+            mq_push<WORK>(d, mq, has, x.s, x.l, w, s_proc, wk);
         }
-        total += __reduce_add_sync(0xFFFFFFFFu, found);
         __syncwarp();
-    }
-    if (lane == 0 && total) {
-        atomicAdd(&d.local[x.u], (unsigned long long)total);
-        atomicAdd(&d.local[x.v], (unsigned long long)total);
     }
 }
 
 template <int TILE, bool WORK>
 __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, const BatchDev& b, int cls,
-                                               unsigned long long* s_proc, Work& wk) {
+                                               unsigned long long* s_proc, MatchQueue& mq, Work& wk) {
     constexpr uint32_t kPerWarp = 32 / TILE, kRounds = 4, kGrab = kPerWarp * kRounds;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long count = d.ctrl->bin_count[cls];
@@ -438,14 +512,15 @@ __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, const BatchDe
         for (uint32_t r = 0; r < kRounds; ++r) {
             const unsigned long long i = base + r * kPerWarp + lane / TILE;
             const bool valid = i < count;
-            intersect_tile<TILE, WORK>(d, b, valid ? items[i] : 0u, valid, s_proc, wk);
+            intersect_tile<TILE, WORK>(d, b, valid ? items[i] : 0u, valid, s_proc, mq, wk);
         }
     }
 }
 
 template <bool WORK>
 __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, const BatchDev& b, int cls,
-                                               unsigned long long* s_proc, uint32_t* queue, Work& wk) {
+                                               unsigned long long* s_proc, uint32_t* queue, MatchQueue& mq,
+                                               Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long count = d.ctrl->bin_count[cls];
     const uint32_t* items = d.items + d.ctrl->bin_start[cls];
@@ -454,7 +529,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, const BatchDe
         if (lane == 0) i = atomicAdd(&d.ctrl->bin_next[cls], 1ull);
         i = __shfl_sync(0xFFFFFFFFu, i, 0);
         if (i >= count) break;
-        intersect_warp<WORK>(d, b, items[i], s_proc, queue, wk);
+        intersect_warp<WORK>(d, b, items[i], s_proc, queue, mq, wk);
     }
 }
 
@@ -465,18 +540,22 @@ template <bool WORK>
 __global__ void __launch_bounds__(256, 4) k_intersect(StreamDev d, BatchDev b) {
     extern __shared__ unsigned long long s_proc[];
     __shared__ uint32_t s_queue[256 / 32][kQueue];
+    __shared__ uint32_t s_match[256 / 32][3][kMatchQ];
     for (uint32_t i = threadIdx.x; i < d.c; i += blockDim.x) s_proc[i] = 0ull;
     __syncthreads();
     const unsigned lane = threadIdx.x & 31u;
-    uint32_t* queue = s_queue[threadIdx.x >> 5];
+    const unsigned wid = threadIdx.x >> 5;
+    uint32_t* queue = s_queue[wid];
+    MatchQueue mq{s_match[wid][0], s_match[wid][1], s_match[wid][2], 0u};
     Work wk;
     if (d.ctrl->status == 0u) {
-        drain_warp_bin<WORK>(d, b, 5, s_proc, queue, wk);
-        drain_warp_bin<WORK>(d, b, 4, s_proc, queue, wk);
-        drain_tile_bin<32, WORK>(d, b, 3, s_proc, wk);
-        drain_tile_bin<16, WORK>(d, b, 2, s_proc, wk);
-        drain_tile_bin<8, WORK>(d, b, 1, s_proc, wk);
-        drain_tile_bin<4, WORK>(d, b, 0, s_proc, wk);
+        drain_warp_bin<WORK>(d, b, 5, s_proc, queue, mq, wk);
+        drain_warp_bin<WORK>(d, b, 4, s_proc, queue, mq, wk);
+        drain_tile_bin<32, WORK>(d, b, 3, s_proc, mq, wk);
+        drain_tile_bin<16, WORK>(d, b, 2, s_proc, mq, wk);
+        drain_tile_bin<8, WORK>(d, b, 1, s_proc, mq, wk);
+        drain_tile_bin<4, WORK>(d, b, 0, s_proc, mq, wk);
+        if (mq.n) mq_flush<WORK>(d, mq, mq.n, s_proc, wk);
     }
     if (WORK) {
         for (int o = 16; o > 0; o >>= 1) {

@@ -103,6 +103,7 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
     d.touched = reinterpret_cast<uint32_t*>(sc + L.touched);
     d.grow_rel = reinterpret_cast<uint32_t*>(sc + L.grow_rel);
     d.big = reinterpret_cast<uint32_t*>(sc + L.big);
+    d.big_cap = 2 * (n_edges ? n_edges : 1);
     d.items = reinterpret_cast<uint32_t*>(sc + L.items);
     d.ekey = reinterpret_cast<uint16_t*>(sc + L.ekey);
     d.hist = reinterpret_cast<uint32_t*>(sc + L.hist);
@@ -132,6 +133,7 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
         k_plan<<<grid, threads, 0, st>>>(d);
         k_commit<<<grid, threads, 0, st>>>(d);
         k_rehash_big<<<sms * 4, threads, 0, st>>>(d);
+        k_rehash_huge<<<sms * 2, 1024, 0, st>>>(d);
         k_insert<<<grid, threads, 0, st>>>(d, b);
         k_sort_scan<<<1, 1024, 0, st>>>(d);
         k_sort_scatter<<<grid, threads, 0, st>>>(d, b);
