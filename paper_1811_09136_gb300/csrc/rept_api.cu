@@ -129,15 +129,15 @@ int ensure_batch_scratch(rept_state* s, unsigned long long n, cudaStream_t st) {
     dev_free(s, s->d.touched, 2 * old * sizeof(uint32_t));
     dev_free(s, s->d.grow_rel, 2 * old * sizeof(uint32_t));
     dev_free(s, s->d.big, 2 * old * sizeof(uint32_t));
-    dev_free(s, s->d.items, old * sizeof(uint32_t));
-    dev_free(s, s->d.ekey, old * sizeof(uint16_t));
-    s->d.touched = s->d.grow_rel = s->d.big = s->d.items = nullptr;
-    s->d.ekey = nullptr;
+    dev_free(s, s->d.rec, old * sizeof(WorkItem));
+    dev_free(s, s->d.srec, old * sizeof(WorkItem));
+    s->d.touched = s->d.grow_rel = s->d.big = nullptr;
+    s->d.rec = s->d.srec = nullptr;
     int rc = dev_alloc(s, (void**)&s->d.touched, 2 * n * sizeof(uint32_t));
     if (!rc) rc = dev_alloc(s, (void**)&s->d.grow_rel, 2 * n * sizeof(uint32_t));
     if (!rc) rc = dev_alloc(s, (void**)&s->d.big, 2 * n * sizeof(uint32_t));
-    if (!rc) rc = dev_alloc(s, (void**)&s->d.items, n * sizeof(uint32_t));
-    if (!rc) rc = dev_alloc(s, (void**)&s->d.ekey, n * sizeof(uint16_t));
+    if (!rc) rc = dev_alloc(s, (void**)&s->d.rec, n * sizeof(WorkItem));
+    if (!rc) rc = dev_alloc(s, (void**)&s->d.srec, n * sizeof(WorkItem));
     if (rc) return rc;
     s->max_batch = n;
     s->d.big_cap = 2 * n;
@@ -479,8 +479,8 @@ void rept_destroy(rept_state* s) {
     cudaFree(d.touched);
     cudaFree(d.grow_rel);
     cudaFree(d.big);
-    cudaFree(d.items);
-    cudaFree(d.ekey);
+    cudaFree(d.rec);
+    cudaFree(d.srec);
     cudaFree(d.hist);
     cudaFree(s->stage_src);
     cudaFree(s->stage_dst);

@@ -103,6 +103,17 @@ struct Ctrl {
     unsigned long long huge_next;
 };
 
+// What k_intersect needs about one arriving edge t = (s, l), s the endpoint with the smaller table:
+// both tables' offsets (in 4-slot units) and sizes, written by k_insert once the batch's tables are
+// final, then moved into sorted order by k_sort_scatter.
+struct __align__(16) WorkItem {
+    uint32_t s, l, off_s, off_l;
+    uint32_t t;      // stream index of the edge
+    uint32_t lgs;    // log2 table sizes: smaller | larger << 8
+    uint32_t cnt_s;  // entries in the smaller table
+    uint32_t key;    // work class * kKeyBuckets + hash of l, or kNoKey
+};
+
 // Everything a kernel needs to know about one stream's state.
 struct StreamDev {
     uint32_t m, c, groups, n_nodes;
@@ -116,9 +127,9 @@ struct StreamDev {
     uint32_t* add;
     uint32_t* touched;
     uint32_t* grow_rel;
-    uint16_t* ekey;     // [max_batch] work-class/sort key of each edge, kNoKey if it closes no wedge
-    uint32_t* hist;     // [kSortBuckets] counts, then cursors, of the counting sort by key
-    uint32_t* items;    // [max_batch] edge indices (batch-relative) sorted by key
+    struct WorkItem* rec;   // [max_batch] work record of each edge (key kNoKey if it closes no wedge)
+    struct WorkItem* srec;  // [max_batch] the records of edges that can close wedges, sorted by key
+    uint32_t* hist;         // [kSortBuckets] counts, then cursors, of the counting sort by key
     uint32_t* big;      // [big_cap] touched-list indices of nodes with a large table to move: the
                         // k_rehash_big list from the front, the k_rehash_huge list from the back
     unsigned long long big_cap;

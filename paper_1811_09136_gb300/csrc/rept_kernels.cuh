@@ -223,6 +223,7 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
         const bool loop = valid && u == v;
         const bool kept = valid && u != v && kept_by_any(d, u, v);
         uint32_t key = kNoKey;
+        WorkItem it{};
         if (valid && u != v) {
             const uint2 mu = d.meta[u], mv = d.meta[v];
             if (kept) {
@@ -234,12 +235,19 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
             // an edge can close wedges only if both endpoints have stored edges
             if (mu.y != 0u && mv.y != 0u) {
                 const bool u_small = mu.y <= mv.y;
-                const uint32_t l = u_small ? v : u;
-                key = (uint32_t)bin_of(table_lg(u_small ? mu.y : mv.y)) * kKeyBuckets +
-                      ((l * 0x9E3779B1u) >> (32 - kKeyBits));
+                const uint2 ms = u_small ? mu : mv, ml = u_small ? mv : mu;
+                it.s = u_small ? u : v;
+                it.l = u_small ? v : u;
+                it.off_s = ms.x;
+                it.off_l = ml.x;
+                it.t = (uint32_t)(b.t0 + e);
+                it.lgs = table_lg(ms.y) | (table_lg(ml.y) << 8);
+                it.cnt_s = ms.y;
+                key = (uint32_t)bin_of(table_lg(ms.y)) * kKeyBuckets + ((it.l * 0x9E3779B1u) >> (32 - kKeyBits));
             }
         }
-        if (valid) d.ekey[e] = (uint16_t)key;
+        it.key = key;
+        if (valid) d.rec[e] = it;
         {
             const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
             if (key != kNoKey && lane == (unsigned)(__ffs(peers) - 1))
@@ -308,13 +316,16 @@ __global__ void k_sort_scatter(StreamDev d, BatchDev b) {
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < b.n;
          base += stride) {
         const unsigned long long e = base + lane;
-        const uint32_t key = e < b.n ? (uint32_t)d.ekey[e] : (uint32_t)kNoKey;
+        WorkItem it{};
+        it.key = kNoKey;
+        if (e < b.n) it = d.rec[e];
+        const uint32_t key = it.key;
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
         const int leader = __ffs(peers) - 1;
         uint32_t pos = 0;
         if (key != kNoKey && (int)lane == leader) pos = atomicAdd(&d.hist[key], (uint32_t)__popc(peers));
         pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-        if (key != kNoKey) d.items[pos + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)e;
+        if (key != kNoKey) d.srec[pos + __popc(peers & ((1u << lane) - 1u))] = it;
     }
 }
 
@@ -406,41 +417,19 @@ __device__ __forceinline__ void mq_push(const StreamDev& d, MatchQueue& q, bool 
     if (q.n >= 32u) mq_flush<WORK>(d, q, 32u, s_proc, wk);
 }
 
-// The endpoints of edge e in the order (smaller table, larger table).
-struct EdgeView {
-    uint32_t u, v, s, l, t;
-    uint2 ms, ml;
-};
-
-__device__ __forceinline__ EdgeView edge_view(const StreamDev& d, const BatchDev& b, uint32_t e) {
-    EdgeView x;
-    x.u = b.src[e];
-    x.v = b.dst[e];
-    x.t = (uint32_t)(b.t0 + e);
-    const uint2 mu = d.meta[x.u], mv = d.meta[x.v];
-    const bool u_small = mu.y <= mv.y;
-    x.s = u_small ? x.u : x.v;
-    x.l = u_small ? x.v : x.u;
-    x.ms = u_small ? mu : mv;
-    x.ml = u_small ? mv : mu;
-    return x;
-}
-
 // Edges whose smaller table has exactly TILE slots: one tile of TILE lanes per edge, one slot per lane.
 template <int TILE, bool WORK>
-__device__ __forceinline__ void intersect_tile(const StreamDev& d, const BatchDev& b, uint32_t e, bool valid,
+__device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkItem& x, bool valid,
                                                unsigned long long* s_proc, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u, j = lane & (TILE - 1);
     bool has = false;
     uint32_t w = 0;
-    EdgeView x{};
     if (valid) {
-        x = edge_view(d, b, e);
-        const uint2 es = d.pool[4ull * x.ms.x + j];
-        if (WORK && j == 0) { wk.entries += x.ms.y; wk.slots += TILE; }
+        const uint2 es = d.pool[4ull * x.off_s + j];
+        if (WORK && j == 0) { wk.entries += x.cnt_s; wk.slots += TILE; }
         if (es.x != kEmptyId && es.y < x.t) {
             uint32_t nslots = 0;
-            const uint32_t tl = table_find(d.pool, 4ull * x.ml.x, table_lg(x.ml.y), es.x, nslots);
+            const uint32_t tl = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, es.x, nslots);
             if (WORK) { ++wk.probes; wk.pslots += nslots; }
             has = tl < x.t;  // kEmptyId (absent) is never < t
             w = es.x;
@@ -455,14 +444,12 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const BatchDe
 constexpr int kQueue = 128;
 
 template <bool WORK>
-__device__ __forceinline__ void intersect_warp(const StreamDev& d, const BatchDev& b, uint32_t e,
-                                               unsigned long long* s_proc, uint32_t* queue, MatchQueue& mq,
-                                               Work& wk) {
+__device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, unsigned long long* s_proc,
+                                               uint32_t* queue, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
-    const EdgeView x = edge_view(d, b, e);
-    const uint32_t cap_s = 1u << table_lg(x.ms.y), lg_l = table_lg(x.ml.y);
-    const unsigned long long base_s = 4ull * x.ms.x, base_l = 4ull * x.ml.x;
-    if (WORK && lane == 0) { wk.entries += x.ms.y; wk.slots += cap_s; }
+    const uint32_t cap_s = 1u << (x.lgs & 0xFFu), lg_l = x.lgs >> 8;
+    const unsigned long long base_s = 4ull * x.off_s, base_l = 4ull * x.off_l;
+    if (WORK && lane == 0) { wk.entries += x.cnt_s; wk.slots += cap_s; }
     const uint4* tab = reinterpret_cast<const uint4*>(d.pool + base_s);  // 32-byte aligned table
     for (uint32_t j0 = 0; j0 < cap_s; j0 += 128u) {
         uint32_t n_q = 0;
@@ -497,12 +484,12 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const BatchDe
 }
 
 template <int TILE, bool WORK>
-__device__ __forceinline__ void drain_tile_bin(const StreamDev& d, const BatchDev& b, int cls,
-                                               unsigned long long* s_proc, MatchQueue& mq, Work& wk) {
+__device__ __forceinline__ void drain_tile_bin(const StreamDev& d, int cls, unsigned long long* s_proc,
+                                               MatchQueue& mq, Work& wk) {
     constexpr uint32_t kPerWarp = 32 / TILE, kRounds = 4, kGrab = kPerWarp * kRounds;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long count = d.ctrl->bin_count[cls];
-    const uint32_t* items = d.items + d.ctrl->bin_start[cls];
+    const WorkItem* items = d.srec + d.ctrl->bin_start[cls];
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(&d.ctrl->bin_next[cls], (unsigned long long)kGrab);
@@ -512,24 +499,26 @@ __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, const BatchDe
         for (uint32_t r = 0; r < kRounds; ++r) {
             const unsigned long long i = base + r * kPerWarp + lane / TILE;
             const bool valid = i < count;
-            intersect_tile<TILE, WORK>(d, b, valid ? items[i] : 0u, valid, s_proc, mq, wk);
+            WorkItem x{};
+            if (valid) x = items[i];
+            intersect_tile<TILE, WORK>(d, x, valid, s_proc, mq, wk);
         }
     }
 }
 
 template <bool WORK>
-__device__ __forceinline__ void drain_warp_bin(const StreamDev& d, const BatchDev& b, int cls,
-                                               unsigned long long* s_proc, uint32_t* queue, MatchQueue& mq,
-                                               Work& wk) {
+__device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, unsigned long long* s_proc,
+                                               uint32_t* queue, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long count = d.ctrl->bin_count[cls];
-    const uint32_t* items = d.items + d.ctrl->bin_start[cls];
+    const WorkItem* items = d.srec + d.ctrl->bin_start[cls];
     for (;;) {
         unsigned long long i = 0;
         if (lane == 0) i = atomicAdd(&d.ctrl->bin_next[cls], 1ull);
         i = __shfl_sync(0xFFFFFFFFu, i, 0);
         if (i >= count) break;
-        intersect_warp<WORK>(d, b, items[i], s_proc, queue, mq, wk);
+        const WorkItem x = items[i];
+        intersect_warp<WORK>(d, x, s_proc, queue, mq, wk);
     }
 }
 
@@ -537,7 +526,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, const BatchDe
 // k_insert; warps claim work dynamically, largest class first.  Dynamic shared memory: c uint64
 // counters (tau^(i) of this block).  WORK = true also tallies the table reads.
 template <bool WORK>
-__global__ void __launch_bounds__(256, 4) k_intersect(StreamDev d, BatchDev b) {
+__global__ void __launch_bounds__(256, 8) k_intersect(StreamDev d, BatchDev b) {
     extern __shared__ unsigned long long s_proc[];
     __shared__ uint32_t s_queue[256 / 32][kQueue];
     __shared__ uint32_t s_match[256 / 32][3][kMatchQ];
@@ -549,12 +538,12 @@ __global__ void __launch_bounds__(256, 4) k_intersect(StreamDev d, BatchDev b) {
     MatchQueue mq{s_match[wid][0], s_match[wid][1], s_match[wid][2], 0u};
     Work wk;
     if (d.ctrl->status == 0u) {
-        drain_warp_bin<WORK>(d, b, 5, s_proc, queue, mq, wk);
-        drain_warp_bin<WORK>(d, b, 4, s_proc, queue, mq, wk);
-        drain_tile_bin<32, WORK>(d, b, 3, s_proc, mq, wk);
-        drain_tile_bin<16, WORK>(d, b, 2, s_proc, mq, wk);
-        drain_tile_bin<8, WORK>(d, b, 1, s_proc, mq, wk);
-        drain_tile_bin<4, WORK>(d, b, 0, s_proc, mq, wk);
+        drain_warp_bin<WORK>(d, 5, s_proc, queue, mq, wk);
+        drain_warp_bin<WORK>(d, 4, s_proc, queue, mq, wk);
+        drain_tile_bin<32, WORK>(d, 3, s_proc, mq, wk);
+        drain_tile_bin<16, WORK>(d, 2, s_proc, mq, wk);
+        drain_tile_bin<8, WORK>(d, 1, s_proc, mq, wk);
+        drain_tile_bin<4, WORK>(d, 0, s_proc, mq, wk);
         if (mq.n) mq_flush<WORK>(d, mq, mq.n, s_proc, wk);
     }
     if (WORK) {

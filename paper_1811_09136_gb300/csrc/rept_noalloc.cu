@@ -25,7 +25,7 @@ inline unsigned long long align256(unsigned long long x) { return (x + 255ull) &
 
 // Offsets of the state inside the scratch area for n nodes and E edges.
 struct Layout {
-    unsigned long long meta, add, touched, grow_rel, big, items, ekey, hist, ctrl, pool, end;
+    unsigned long long meta, add, touched, grow_rel, big, rec, srec, hist, ctrl, pool, end;
     unsigned long long pool_quads;
 };
 
@@ -37,8 +37,8 @@ Layout layout_for(unsigned long long n, unsigned long long E) {
     L.touched = o;  o = align256(o + 2 * E * sizeof(uint32_t));
     L.grow_rel = o; o = align256(o + 2 * E * sizeof(uint32_t));
     L.big = o;      o = align256(o + 2 * E * sizeof(uint32_t));
-    L.items = o;    o = align256(o + E * sizeof(uint32_t));
-    L.ekey = o;     o = align256(o + E * sizeof(uint16_t));
+    L.rec = o;      o = align256(o + E * sizeof(WorkItem));
+    L.srec = o;     o = align256(o + E * sizeof(WorkItem));
     L.hist = o;     o = align256(o + kSortBuckets * sizeof(uint32_t));
     L.ctrl = o;     o = align256(o + sizeof(Ctrl));
     // From an empty state every node's table is allocated once, with at most 4 slots per entry:
@@ -104,8 +104,8 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
     d.grow_rel = reinterpret_cast<uint32_t*>(sc + L.grow_rel);
     d.big = reinterpret_cast<uint32_t*>(sc + L.big);
     d.big_cap = 2 * (n_edges ? n_edges : 1);
-    d.items = reinterpret_cast<uint32_t*>(sc + L.items);
-    d.ekey = reinterpret_cast<uint16_t*>(sc + L.ekey);
+    d.rec = reinterpret_cast<WorkItem*>(sc + L.rec);
+    d.srec = reinterpret_cast<WorkItem*>(sc + L.srec);
     d.hist = reinterpret_cast<uint32_t*>(sc + L.hist);
     d.ctrl = reinterpret_cast<Ctrl*>(sc + L.ctrl);
     d.pool = reinterpret_cast<uint2*>(sc + L.pool);
