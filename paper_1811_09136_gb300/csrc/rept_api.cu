@@ -336,7 +336,7 @@ int rept_ingest_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_ds
     if (!s) return REPT_E_INVAL;
     if (n == 0) return REPT_OK;
     if (!d_src || !d_dst) return REPT_E_INVAL;
-    if (s->next_t + n >= 0xFFFFFFFFull) return REPT_E_INVAL;  // stream indices are 32-bit
+    if (s->next_t + n >= 0xFFFFFFFEull) return REPT_E_INVAL;  // stream indices stay below 2^32 - 2
     cudaStream_t st = as_stream(stream);
     int rc = ensure_batch_scratch(s, n, st);
     if (rc) return rc;
@@ -369,7 +369,7 @@ int rept_ingest_host(rept_state* s, const uint32_t* h_src, const uint32_t* h_dst
         const unsigned long long k = std::min<unsigned long long>(chunk, n - off);
         REPT_CUDA(cudaMemcpyAsync(s->stage_src, h_src + off, k * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
         REPT_CUDA(cudaMemcpyAsync(s->stage_dst, h_dst + off, k * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-        if (s->next_t + k >= 0xFFFFFFFFull) return REPT_E_INVAL;
+        if (s->next_t + k >= 0xFFFFFFFEull) return REPT_E_INVAL;
         rc = launch_batch(s, s->stage_src, s->stage_dst, k, st);
         if (rc) return rc;
     }

@@ -443,41 +443,93 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
 // shared-memory key queue, and then probes them with all 32 lanes.
 constexpr int kQueue = 128;
 
+// The lookup of w once its home bucket (p0, p1) has been read: the stream index if w is in the bucket,
+// kEmptyId if the bucket shows w absent, and kReadOn if the bucket is full without w.  Stream indices
+// stay below 2^32 - 2 (the host rejects longer streams), so kReadOn is never an index.
+constexpr uint32_t kReadOn = 0xFFFFFFFEu;
+
+__device__ __forceinline__ uint32_t bucket_lookup(const uint4& p0, const uint4& p1, uint32_t w) {
+    if (p0.x == w) return p0.y;
+    if (p0.z == w) return p0.w;
+    if (p1.x == w) return p1.y;
+    if (p1.z == w) return p1.w;
+    if (p0.x == kEmptyId || p0.z == kEmptyId || p1.x == kEmptyId || p1.z == kEmptyId) return kEmptyId;
+    return kReadOn;
+}
+
+// table_find from the bucket after w's home bucket (the home bucket was full without w).
+__device__ __forceinline__ uint32_t table_find_after_home(const uint2* __restrict__ pool, unsigned long long base,
+                                                          uint32_t lg, uint32_t w, uint32_t& slots) {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = (home_slot(w, lg) + 4u) & mask;
+    const uint4* tab = reinterpret_cast<const uint4*>(pool + base);
+    slots = 4u;
+    for (uint32_t probe = 4; probe <= mask; probe += 4u) {
+        const uint4 p0 = tab[h >> 1], p1 = tab[(h >> 1) + 1];
+        slots = probe + 4u;
+        const uint32_t r = bucket_lookup(p0, p1, w);
+        if (r != kReadOn) return r;
+        h = (h + 4u) & mask;
+    }
+    return kEmptyId;
+}
+
 template <bool WORK>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, unsigned long long* s_proc,
                                                uint32_t* queue, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const uint32_t cap_s = 1u << (x.lgs & 0xFFu), lg_l = x.lgs >> 8;
-    const unsigned long long base_s = 4ull * x.off_s, base_l = 4ull * x.off_l;
+    const unsigned long long base_l = 4ull * x.off_l;
     if (WORK && lane == 0) { wk.entries += x.cnt_s; wk.slots += cap_s; }
-    const uint4* tab = reinterpret_cast<const uint4*>(d.pool + base_s);  // 32-byte aligned table
+    const uint4* tab = reinterpret_cast<const uint4*>(d.pool + 4ull * x.off_s);  // 32-byte aligned tables
+    const uint4* tab_l = reinterpret_cast<const uint4*>(d.pool + base_l);
+    const uint4 none = make_uint4(kEmptyId, 0u, kEmptyId, 0u);
+    // 128 slots per pass, two per lane per 16-byte load; the next pass's loads are issued before
+    // this pass's probes (cap_s is a multiple of 64)
+    uint4 qa = tab[lane];
+    uint4 qb = 64u < cap_s ? tab[32 + lane] : none;
     for (uint32_t j0 = 0; j0 < cap_s; j0 += 128u) {
         uint32_t n_q = 0;
+        const unsigned below = (1u << lane) - 1u;
 #pragma unroll
-        for (uint32_t half = 0; half < 2; ++half) {
-            const uint32_t jj = j0 + 64u * half;  // cap_s is a multiple of 64
-            uint4 q = make_uint4(kEmptyId, 0u, kEmptyId, 0u);
-            if (jj < cap_s) q = tab[(jj >> 1) + lane];
+        for (int half = 0; half < 2; ++half) {
+            const uint4 q = half ? qb : qa;
             const bool a1 = q.x != kEmptyId && q.y < x.t, a2 = q.z != kEmptyId && q.w < x.t;
             const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
-            const unsigned below = (1u << lane) - 1u;
             if (a1) queue[n_q + __popc(m1 & below)] = q.x;
             n_q += __popc(m1);
             if (a2) queue[n_q + __popc(m2 & below)] = q.z;
             n_q += __popc(m2);
         }
+        const uint32_t jn = j0 + 128u;
+        qa = jn < cap_s ? tab[(jn >> 1) + lane] : none;
+        qb = jn + 64u < cap_s ? tab[((jn + 64u) >> 1) + lane] : none;
         __syncwarp();
-        for (uint32_t k0 = 0; k0 < n_q; k0 += 32u) {
-            bool has = false;
-            uint32_t w = 0;
-            if (k0 + lane < n_q) {
-                w = queue[k0 + lane];
-                uint32_t nslots = 0;
-                const uint32_t tl = table_find(d.pool, base_l, lg_l, w, nslots);
-                if (WORK) { ++wk.probes; wk.pslots += nslots; }
-                has = tl < x.t;
+        // probe two queued neighbours per lane, both home buckets in flight together
+        for (uint32_t k0 = 0; k0 < n_q; k0 += 64u) {
+            const bool v1 = k0 + lane < n_q, v2 = k0 + 32u + lane < n_q;
+            const uint32_t w1 = v1 ? queue[k0 + lane] : 0u, w2 = v2 ? queue[k0 + 32u + lane] : 0u;
+            uint4 a0 = none, a1 = none, b0 = none, b1 = none;
+            if (v1) {
+                const uint32_t h = home_slot(w1, lg_l) >> 1;
+                a0 = tab_l[h];
+                a1 = tab_l[h + 1];
             }
-            mq_push<WORK>(d, mq, has, x.s, x.l, w, s_proc, wk);
+            if (v2) {
+                const uint32_t h = home_slot(w2, lg_l) >> 1;
+                b0 = tab_l[h];
+                b1 = tab_l[h + 1];
+            }
+            uint32_t r1 = bucket_lookup(a0, a1, w1), r2 = bucket_lookup(b0, b1, w2);
+            uint32_t n1 = 4u, n2 = 4u;
+            if (v1 && r1 == kReadOn) r1 = table_find_after_home(d.pool, base_l, lg_l, w1, n1);
+            if (v2 && r2 == kReadOn) r2 = table_find_after_home(d.pool, base_l, lg_l, w2, n2);
+            if (WORK) {
+                if (v1) { ++wk.probes; wk.pslots += n1; }
+                if (v2) { ++wk.probes; wk.pslots += n2; }
+            }
+            mq_push<WORK>(d, mq, v1 && r1 < x.t, x.s, x.l, w1, s_proc, wk);
+            mq_push<WORK>(d, mq, v2 && r2 < x.t, x.s, x.l, w2, s_proc, wk);
         }
         __syncwarp();
     }

@@ -82,7 +82,7 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
     if (c > m && c % m != 0) return REPT_E_INVAL;
     if (c > kMaxProcessors) return REPT_E_INVAL;
     if (n_edges > 0 && (!d_src || !d_dst)) return REPT_E_INVAL;
-    if (n_edges >= 0xFFFFFFFFull) return REPT_E_SCRATCH;
+    if (n_edges >= 0xFFFFFFFEull) return REPT_E_SCRATCH;
     const Layout L = layout_for(n_nodes, n_edges);
     if (L.end > REPT_NOALLOC_SCRATCH_BYTES) return REPT_E_SCRATCH;
     void* base = nullptr;

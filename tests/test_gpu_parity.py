@@ -166,3 +166,20 @@ def test_unsupported_partial_group_rejected():
     from paper_1811_09136_gb300.rept import ReptStream, ReptError
     with pytest.raises(ReptError):
         ReptStream(100, 3, 7, 1)
+
+
+def test_work_counters_match_the_graph():
+    """With m = c = 1 every edge is stored, so the intersection finds every triangle exactly once
+    (at its last edge): wedges == counted == tau.  Probes read whole 4-slot buckets and the tables
+    stay at most half full, so a probe reads few slots on average."""
+    from paper_1811_09136_gb300.rept import ReptStream, FLAG_WORK_COUNTERS
+    s = gg.cached("powerlaw_20k")
+    exact = O.semitriangles(s.src, s.dst, s.n_nodes, 1, 1, 1)
+    src, dst = device_edges(s)
+    with ReptStream(s.n_nodes, 1, 1, 1, max_batch=1 << 15, flags=FLAG_WORK_COUNTERS) as r:
+        for off in range(0, len(s), 1 << 15):
+            r.ingest(src[off:off + (1 << 15)], dst[off:off + (1 << 15)])
+        st = r.stats()
+    assert st["wedges"] == exact.triangles == st["counted"]
+    assert st["probes"] <= st["small_entries"] <= st["small_slots"]
+    assert 4 * st["probes"] <= st["probe_slots"] < 6 * st["probes"]
