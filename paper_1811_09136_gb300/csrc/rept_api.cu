@@ -93,10 +93,10 @@ void dev_free(rept_state* s, void* p, size_t bytes) {
     }
 }
 
-// Pool slots that guarantee no batch can run out: every node's allocations form a
-// doubling series bounded by twice its final capacity, itself at most 4 * cnt, so
-// at most 8 slots per stored entry, i.e. 16 slots (4 quads) per stream edge.
-unsigned long long quads_bound(unsigned long long edges) { return 4ull * edges + 64ull; }
+// Pool slots that guarantee no batch can run out: a node's block (table plus list) holds at
+// most 8 slots per entry, and its successive blocks form a doubling series bounded by twice the
+// last one, so at most 16 slots per stored entry, i.e. 32 slots (8 quads) per stream edge.
+unsigned long long quads_bound(unsigned long long edges) { return 8ull * edges + 64ull; }
 
 int grow_pool(rept_state* s, unsigned long long min_quads, cudaStream_t st) {
     unsigned long long want = std::max(min_quads, 2ull * s->d.pool_quads);

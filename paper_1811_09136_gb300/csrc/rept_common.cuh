@@ -1,14 +1,15 @@
 // Device-side data layout and helpers of the REPT streaming counter.
 //
 // HBM layout of one stream (one rept_state):
-//   meta[n_nodes]   uint2 {off, cnt}: node x's neighbour table starts at slot
-//                   4*off of the pool and holds cnt entries; its capacity is a
-//                   function of cnt alone (table_lg below), so a node's table
-//                   is re-allocated exactly when cnt crosses a power-of-two
+//   meta[n_nodes]   uint2 {off, cnt}: node x's block starts at slot 4*off of
+//                   the pool and holds cnt entries; its size is a function of
+//                   cnt alone (table_lg below), so a node's block is
+//                   re-allocated exactly when cnt crosses a power-of-two
 //                   boundary.
-//   pool[]          uint2 slots {nbr, eidx}: one open-addressing (linear
-//                   probing) table per node, keyed by the neighbour id.  An
-//                   entry (w, t) in x's table is the stored edge {x, w} that
+//   pool[]          uint2 slots {nbr, eidx}: per node, an open-addressing
+//                   (linear probing, 4-slot buckets) table keyed by the
+//                   neighbour id, followed by the same entries as a packed
+//                   list.  An entry (w, t) of x is the stored edge {x, w} that
 //                   arrived at stream index t.  Empty slots are all-ones.  The
 //                   tables of all processors share one union adjacency: an
 //                   edge is stored once if any processor keeps it, and which
@@ -30,10 +31,8 @@ constexpr unsigned long long kEmptySlot = 0xFFFFFFFFFFFFFFFFull;
 constexpr uint64_t kGoldenGamma = 0x9E3779B97F4A7C15ull;  // SplitMix64 increment
 constexpr uint32_t kNoGrow = 0xFFFFFFFFu;
 constexpr uint32_t kMaxProcessors = 4096;  // per-block tau^(i) histogram lives in shared memory
-// k_intersect work classes by the smaller endpoint's table size 2^lg: lg 2..5 are handled by
-// tiles of 4, 8, 16, 32 lanes (one slot per lane), 64..512 slots and >= 1024 slots by a warp.
+// Number of k_intersect work classes (see bin_of_cnt).
 constexpr int kBins = 6;
-__host__ __device__ __forceinline__ int bin_of(uint32_t lg_s) { return lg_s <= 5u ? (int)lg_s - 2 : (lg_s <= 9u ? 4 : 5); }
 // Within a class, work items are ordered by a hash of the larger endpoint (kKeyBits bits), so that
 // the edges probing the same large table run back to back and find it in L2.
 constexpr int kKeyBits = 13;
@@ -110,7 +109,7 @@ struct __align__(16) WorkItem {
     uint32_t s, l, off_s, off_l;
     uint32_t t;      // stream index of the edge
     uint32_t lgs;    // log2 table sizes: smaller | larger << 8
-    uint32_t cnt_s;  // entries in the smaller table
+    uint32_t cnt_s;  // entries of the smaller endpoint
     uint32_t key;    // work class * kKeyBuckets + hash of l, or kNoKey
 };
 
@@ -179,6 +178,18 @@ __host__ __device__ __forceinline__ uint32_t table_lg(uint32_t cnt) {
     uint32_t lg = 32u - (uint32_t)__builtin_clz(x);
 #endif
     return lg < 2u ? 2u : lg;
+}
+
+// A node's block in the pool: its hash table (2^lg slots, probed by neighbour id) followed by its
+// entry list (list_slots(lg) slots, the same entries packed in insertion order, scanned when the
+// node is the smaller endpoint).  Both parts are multiples of 4 slots (32 bytes).
+__host__ __device__ __forceinline__ uint32_t list_slots(uint32_t lg) { return lg >= 3u ? (1u << (lg - 1u)) : 4u; }
+__host__ __device__ __forceinline__ uint32_t block_quads(uint32_t lg) { return ((1u << lg) + list_slots(lg)) >> 2; }
+
+// k_intersect work class of an edge whose smaller endpoint holds cnt entries: tiles of 4, 8, 16, 32
+// lanes (one entry per lane), then a warp per edge for up to 256 entries and for more.
+__host__ __device__ __forceinline__ int bin_of_cnt(uint32_t cnt) {
+    return cnt <= 4u ? 0 : cnt <= 8u ? 1 : cnt <= 16u ? 2 : cnt <= 32u ? 3 : cnt <= 256u ? 4 : 5;
 }
 
 // Home slot of neighbour w in a table of 2^lg slots: the first slot of a 4-slot (32-byte) bucket

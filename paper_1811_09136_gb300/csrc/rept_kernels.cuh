@@ -79,15 +79,32 @@ __global__ void k_plan(StreamDev d) {
             const uint32_t x = d.touched[i];
             const uint32_t cnt = d.meta[x].y, add = d.add[x];
             const uint32_t lg_old = table_lg(cnt), lg_new = table_lg(cnt + add);
-            if (lg_new != lg_old) need = (1ull << lg_new) >> 2;
+            if (lg_new != lg_old) need = block_quads(lg_new);
         }
         const unsigned long long rel = warp_reserve(&d.ctrl->need_quads, need);
         if (valid) d.grow_rel[i] = need ? (uint32_t)rel : kNoGrow;
     }
 }
 
-// Publish the new entry counts of the touched nodes and move the tables that were re-allocated.
-// One thread per touched node; a table of more than 16 slots is left to k_rehash_big (a warp each).
+// Move node x's entries (list of cnt_old entries at old_off) into its new block at new_off: copy the
+// list and insert each entry into the new table.  Lanes `rank` of `width` share the work.
+__device__ __forceinline__ bool move_block(uint2* pool, uint32_t old_off, uint32_t cnt_old, unsigned long long new_off,
+                                           uint32_t lg_new, uint32_t rank, uint32_t width) {
+    const uint2* old_list = pool + 4ull * old_off + (1ull << table_lg(cnt_old));
+    uint2* new_list = pool + 4ull * new_off + (1ull << lg_new);
+    bool ok = true;
+    for (uint32_t j = rank; j < cnt_old; j += width) {
+        const uint2 e = old_list[j];
+        new_list[j] = e;
+        ok &= table_insert(pool, 4ull * new_off, lg_new, e.x, e.y);
+    }
+    return ok;
+}
+
+// Publish the new entry counts of the touched nodes and move the blocks that were re-allocated.
+// One thread per touched node; a block holding more than 8 entries is left to k_rehash_big (a warp
+// each) or k_rehash_huge (a thread block each).  add[x] keeps the batch's new-entry count for
+// k_insert, which counts it back down to zero; a batch that is not applied clears it here.
 __global__ void k_commit(StreamDev d) {
     const unsigned status = d.ctrl->status;
     const unsigned long long n_t = d.ctrl->n_touched;
@@ -102,33 +119,24 @@ __global__ void k_commit(StreamDev d) {
         bool defer = false, huge = false;
         if (i < n_t) {
             const uint32_t x = d.touched[i];
-            bool done = true;
-            if (!bad) {
+            if (bad) {
+                d.add[x] = 0u;
+            } else {
                 const uint2 m = d.meta[x];
                 const uint32_t cnt_new = m.y + d.add[x];
                 const uint32_t rel = d.grow_rel[i];
                 if (rel == kNoGrow) {
                     d.meta[x].y = cnt_new;
+                } else if (m.y > 8u) {
+                    defer = m.y <= 2048u;
+                    huge = !defer;
                 } else {
                     const unsigned long long new_off = top + rel;
-                    const uint32_t lg_old = table_lg(m.y);
-                    if (lg_old > 4u) {
-                        defer = lg_old <= 11u;
-                        huge = !defer;
-                        done = false;
-                    } else {
-                        bool ok = true;
-                        const uint32_t lg_new = table_lg(cnt_new);
-                        for (uint32_t j = 0; m.y > 0u && j < (1u << lg_old); ++j) {
-                            const uint2 sl = d.pool[4ull * m.x + j];
-                            if (sl.x != kEmptyId) ok &= table_insert(d.pool, 4ull * new_off, lg_new, sl.x, sl.y);
-                        }
-                        if (!ok) atomicOr(&d.ctrl->status, kStInternal);
-                        d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
-                    }
+                    if (!move_block(d.pool, m.x, m.y, new_off, table_lg(cnt_new), 0u, 1u))
+                        atomicOr(&d.ctrl->status, kStInternal);
+                    d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
                 }
             }
-            if (done) d.add[x] = 0u;
         }
         const unsigned long long o = warp_reserve(&d.ctrl->n_big, defer ? 1ull : 0ull);
         if (defer) d.big[o] = (uint32_t)i;
@@ -137,7 +145,7 @@ __global__ void k_commit(StreamDev d) {
     }
 }
 
-// Move the large tables listed by k_commit: one warp per node.
+// Move the blocks of 9..2048 entries listed by k_commit: one warp per node.
 __global__ void k_rehash_big(StreamDev d) {
     const unsigned long long n_big = d.ctrl->n_big, top = d.ctrl->pool_top;
     const unsigned lane = threadIdx.x & 31u;
@@ -149,22 +157,14 @@ __global__ void k_rehash_big(StreamDev d) {
         const uint2 m = d.meta[x];
         const uint32_t cnt_new = m.y + d.add[x];
         const unsigned long long new_off = top + d.grow_rel[i];
-        const uint32_t lg_new = table_lg(cnt_new), old_cap = 1u << table_lg(m.y);
-        bool ok = true;
-        for (uint32_t j = lane; j < old_cap; j += 32u) {
-            const uint2 sl = d.pool[4ull * m.x + j];
-            if (sl.x != kEmptyId) ok &= table_insert(d.pool, 4ull * new_off, lg_new, sl.x, sl.y);
-        }
-        if (!ok) atomicOr(&d.ctrl->status, kStInternal);
+        if (!move_block(d.pool, m.x, m.y, new_off, table_lg(cnt_new), lane, 32u))
+            atomicOr(&d.ctrl->status, kStInternal);
         __syncwarp();
-        if (lane == 0) {
-            d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
-            d.add[x] = 0u;
-        }
+        if (lane == 0) d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
     }
 }
 
-// Move the tables of >= 4096 slots listed by k_commit: blocks claim one node at a time.
+// Move the blocks of more than 2048 entries listed by k_commit: thread blocks claim one node at a time.
 __global__ void __launch_bounds__(1024) k_rehash_huge(StreamDev d) {
     __shared__ unsigned long long s_k;
     __shared__ int s_bad;
@@ -182,18 +182,11 @@ __global__ void __launch_bounds__(1024) k_rehash_huge(StreamDev d) {
         const uint2 m = d.meta[x];
         const uint32_t cnt_new = m.y + d.add[x];
         const unsigned long long new_off = top + d.grow_rel[i];
-        const uint32_t lg_new = table_lg(cnt_new), old_cap = 1u << table_lg(m.y);
-        bool ok = true;
-        for (uint32_t j = threadIdx.x; j < old_cap; j += blockDim.x) {
-            const uint2 sl = d.pool[4ull * m.x + j];
-            if (sl.x != kEmptyId) ok &= table_insert(d.pool, 4ull * new_off, lg_new, sl.x, sl.y);
-        }
-        if (!ok) s_bad = 1;
+        if (!move_block(d.pool, m.x, m.y, new_off, table_lg(cnt_new), threadIdx.x, blockDim.x)) s_bad = 1;
         __syncthreads();
         if (threadIdx.x == 0) {
             if (s_bad) atomicOr(&d.ctrl->status, kStInternal);
             d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
-            d.add[x] = 0u;
         }
         __syncthreads();
     }
@@ -228,9 +221,14 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
             const uint2 mu = d.meta[u], mv = d.meta[v];
             if (kept) {
                 const uint32_t t = (uint32_t)(b.t0 + e);
-                bool ok = table_insert(d.pool, 4ull * mu.x, table_lg(mu.y), v, t);
-                ok &= table_insert(d.pool, 4ull * mv.x, table_lg(mv.y), u, t);
+                const uint32_t lu = table_lg(mu.y), lv = table_lg(mv.y);
+                bool ok = table_insert(d.pool, 4ull * mu.x, lu, v, t);
+                ok &= table_insert(d.pool, 4ull * mv.x, lv, u, t);
                 if (!ok) atomicOr(&ct->status, kStInternal);
+                // list positions: add[x] counts this batch's entries of x back down to zero
+                const uint32_t pu = mu.y - atomicSub(&d.add[u], 1u), pv = mv.y - atomicSub(&d.add[v], 1u);
+                d.pool[4ull * mu.x + (1ull << lu) + pu] = make_uint2(v, t);
+                d.pool[4ull * mv.x + (1ull << lv) + pv] = make_uint2(u, t);
             }
             // an edge can close wedges only if both endpoints have stored edges
             if (mu.y != 0u && mv.y != 0u) {
@@ -243,7 +241,7 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
                 it.t = (uint32_t)(b.t0 + e);
                 it.lgs = table_lg(ms.y) | (table_lg(ml.y) << 8);
                 it.cnt_s = ms.y;
-                key = (uint32_t)bin_of(table_lg(ms.y)) * kKeyBuckets + ((it.l * 0x9E3779B1u) >> (32 - kKeyBits));
+                key = (uint32_t)bin_of_cnt(ms.y) * kKeyBuckets + ((it.l * 0x9E3779B1u) >> (32 - kKeyBits));
             }
         }
         it.key = key;
@@ -417,17 +415,18 @@ __device__ __forceinline__ void mq_push(const StreamDev& d, MatchQueue& q, bool 
     if (q.n >= 32u) mq_flush<WORK>(d, q, 32u, s_proc, wk);
 }
 
-// Edges whose smaller table has exactly TILE slots: one tile of TILE lanes per edge, one slot per lane.
+// Edges whose smaller endpoint has at most TILE entries: one tile of TILE lanes per edge, one list
+// entry per lane.
 template <int TILE, bool WORK>
 __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkItem& x, bool valid,
                                                unsigned long long* s_proc, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u, j = lane & (TILE - 1);
     bool has = false;
     uint32_t w = 0;
-    if (valid) {
-        const uint2 es = d.pool[4ull * x.off_s + j];
-        if (WORK && j == 0) { wk.entries += x.cnt_s; wk.slots += TILE; }
-        if (es.x != kEmptyId && es.y < x.t) {
+    if (valid && j < x.cnt_s) {
+        const uint2 es = d.pool[4ull * x.off_s + (1ull << (x.lgs & 0xFFu)) + j];
+        if (WORK && j == 0) { wk.entries += x.cnt_s; wk.slots += x.cnt_s; }
+        if (es.y < x.t) {
             uint32_t nslots = 0;
             const uint32_t tl = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, es.x, nslots);
             if (WORK) { ++wk.probes; wk.pslots += nslots; }
@@ -478,58 +477,38 @@ template <bool WORK>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, unsigned long long* s_proc,
                                                uint32_t* queue, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
-    const uint32_t cap_s = 1u << (x.lgs & 0xFFu), lg_l = x.lgs >> 8;
+    const uint32_t lg_l = x.lgs >> 8, n_s = x.cnt_s;
     const unsigned long long base_l = 4ull * x.off_l;
-    if (WORK && lane == 0) { wk.entries += x.cnt_s; wk.slots += cap_s; }
-    const uint4* tab = reinterpret_cast<const uint4*>(d.pool + 4ull * x.off_s);  // 32-byte aligned tables
-    const uint4* tab_l = reinterpret_cast<const uint4*>(d.pool + base_l);
-    const uint4 none = make_uint4(kEmptyId, 0u, kEmptyId, 0u);
-    // 128 slots per pass, two per lane per 16-byte load; the next pass's loads are issued before
-    // this pass's probes (cap_s is a multiple of 64)
-    uint4 qa = tab[lane];
-    uint4 qb = 64u < cap_s ? tab[32 + lane] : none;
-    for (uint32_t j0 = 0; j0 < cap_s; j0 += 128u) {
+    if (WORK && lane == 0) { wk.entries += n_s; wk.slots += n_s; }
+    // the smaller endpoint's entry list (32-byte aligned), read 128 entries per pass, two per 16-byte load
+    const uint4* list = reinterpret_cast<const uint4*>(d.pool + 4ull * x.off_s + (1ull << (x.lgs & 0xFFu)));
+    for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
         uint32_t n_q = 0;
         const unsigned below = (1u << lane) - 1u;
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const uint4 q = half ? qb : qa;
-            const bool a1 = q.x != kEmptyId && q.y < x.t, a2 = q.z != kEmptyId && q.w < x.t;
+        for (uint32_t half = 0; half < 2; ++half) {
+            const uint32_t jj = j0 + 64u * half + 2u * lane;
+            uint4 q = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
+            if (jj < n_s) q = list[jj >> 1];
+            const bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
             const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
             if (a1) queue[n_q + __popc(m1 & below)] = q.x;
             n_q += __popc(m1);
             if (a2) queue[n_q + __popc(m2 & below)] = q.z;
             n_q += __popc(m2);
         }
-        const uint32_t jn = j0 + 128u;
-        qa = jn < cap_s ? tab[(jn >> 1) + lane] : none;
-        qb = jn + 64u < cap_s ? tab[((jn + 64u) >> 1) + lane] : none;
         __syncwarp();
-        // probe two queued neighbours per lane, both home buckets in flight together
-        for (uint32_t k0 = 0; k0 < n_q; k0 += 64u) {
-            const bool v1 = k0 + lane < n_q, v2 = k0 + 32u + lane < n_q;
-            const uint32_t w1 = v1 ? queue[k0 + lane] : 0u, w2 = v2 ? queue[k0 + 32u + lane] : 0u;
-            uint4 a0 = none, a1 = none, b0 = none, b1 = none;
-            if (v1) {
-                const uint32_t h = home_slot(w1, lg_l) >> 1;
-                a0 = tab_l[h];
-                a1 = tab_l[h + 1];
+        for (uint32_t k0 = 0; k0 < n_q; k0 += 32u) {
+            bool has = false;
+            uint32_t w = 0;
+            if (k0 + lane < n_q) {
+                w = queue[k0 + lane];
+                uint32_t nslots = 0;
+                const uint32_t tl = table_find(d.pool, base_l, lg_l, w, nslots);
+                if (WORK) { ++wk.probes; wk.pslots += nslots; }
+                has = tl < x.t;
             }
-            if (v2) {
-                const uint32_t h = home_slot(w2, lg_l) >> 1;
-                b0 = tab_l[h];
-                b1 = tab_l[h + 1];
-            }
-            uint32_t r1 = bucket_lookup(a0, a1, w1), r2 = bucket_lookup(b0, b1, w2);
-            uint32_t n1 = 4u, n2 = 4u;
-            if (v1 && r1 == kReadOn) r1 = table_find_after_home(d.pool, base_l, lg_l, w1, n1);
-            if (v2 && r2 == kReadOn) r2 = table_find_after_home(d.pool, base_l, lg_l, w2, n2);
-            if (WORK) {
-                if (v1) { ++wk.probes; wk.pslots += n1; }
-                if (v2) { ++wk.probes; wk.pslots += n2; }
-            }
-            mq_push<WORK>(d, mq, v1 && r1 < x.t, x.s, x.l, w1, s_proc, wk);
-            mq_push<WORK>(d, mq, v2 && r2 < x.t, x.s, x.l, w2, s_proc, wk);
+            mq_push<WORK>(d, mq, has, x.s, x.l, w, s_proc, wk);
         }
         __syncwarp();
     }

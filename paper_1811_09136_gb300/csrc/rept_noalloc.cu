@@ -41,9 +41,9 @@ Layout layout_for(unsigned long long n, unsigned long long E) {
     L.srec = o;     o = align256(o + E * sizeof(WorkItem));
     L.hist = o;     o = align256(o + kSortBuckets * sizeof(uint32_t));
     L.ctrl = o;     o = align256(o + sizeof(Ctrl));
-    // From an empty state every node's table is allocated once, with at most 4 slots per entry:
-    // at most 8 slots (2 quads) per edge.
-    L.pool_quads = 2 * E + 1;
+    // From an empty state every node's block (table plus list) is allocated once, with at most 8
+    // slots per entry: at most 16 slots (4 quads) per edge.
+    L.pool_quads = 4 * E + 1;
     L.pool = o;     o = align256(o + L.pool_quads * 32ull);
     L.end = o;
     return L;
