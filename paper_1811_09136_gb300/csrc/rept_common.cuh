@@ -6,11 +6,12 @@
 //                   cnt alone (table_lg below), so a node's block is
 //                   re-allocated exactly when cnt crosses a power-of-two
 //                   boundary.
-//   pool[]          uint2 slots {nbr, eidx}: per node, an open-addressing
-//                   (linear probing, 4-slot buckets) table keyed by the
-//                   neighbour id, followed by the same entries as a packed
-//                   list.  An entry (w, t) of x is the stored edge {x, w} that
-//                   arrived at stream index t.  Empty slots are all-ones.  The
+//   pool[]          8-byte slots: per node, an open-addressing (linear probing,
+//                   4-key buckets) table of 2^lg neighbour ids with a parallel
+//                   array of their stream indices (2^lg slots in all), then
+//                   the same entries as a packed list of {nbr, eidx} pairs.
+//                   An entry (w, t) of x is the stored edge {x, w} that
+//                   arrived at stream index t.  Empty keys are all-ones.  The
 //                   tables of all processors share one union adjacency: an
 //                   edge is stored once if any processor keeps it, and which
 //                   processors keep it is recomputed from the hash when needed

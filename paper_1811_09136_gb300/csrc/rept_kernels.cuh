@@ -22,16 +22,20 @@ namespace rept {
 // Internal linkage: every translation unit of the library that launches these kernels gets its own copy.
 namespace {
 
-// Insert (nbr, eidx) into the table of 2^lg slots starting at slot `base`.  Returns false
-// only if the table has no empty slot left (impossible while cnt <= capacity / 2).
+// A node's table of 2^lg slots at pool slot `base` is two arrays of 2^lg uint32: the neighbour ids
+// (keys; probed a 4-key, 16-byte bucket at a time) and then, at the same positions, the stream index
+// of each entry.  Insert (nbr, eidx): claim a key slot with a 32-bit CAS, then store the index.
+// Returns false only if the table has no empty slot left (impossible while cnt <= capacity / 2).
 __device__ __forceinline__ bool table_insert(uint2* pool, unsigned long long base, uint32_t lg, uint32_t nbr,
                                              uint32_t eidx) {
-    unsigned long long* p = reinterpret_cast<unsigned long long*>(pool) + base;
+    uint32_t* keys = reinterpret_cast<uint32_t*>(pool + base);
     const uint32_t mask = (1u << lg) - 1u;
     uint32_t h = home_slot(nbr, lg);
-    const unsigned long long v = pack_slot(nbr, eidx);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
-        if (atomicCAS(p + h, kEmptySlot, v) == kEmptySlot) return true;
+        if (atomicCAS(keys + h, kEmptyId, nbr) == kEmptyId) {
+            keys[(1u << lg) + h] = eidx;
+            return true;
+        }
         h = (h + 1u) & mask;
     }
     return false;
@@ -327,22 +331,25 @@ __global__ void k_sort_scatter(StreamDev d, BatchDev b) {
     }
 }
 
-// Look neighbour w up in the table of 2^lg slots at `base` (lg >= 2): read whole 4-slot buckets
-// from w's home bucket on until w or an empty slot shows up.  Returns w's stream index, or kEmptyId
-// when w is absent; `slots` receives the number of slots read.
+// Look neighbour w up in the table of 2^lg slots at `base` (lg >= 2): read 4-key buckets from w's
+// home bucket on until w or an empty key shows up.  Returns w's stream index, or kEmptyId when w is
+// absent; `slots` receives the number of keys read.
 __device__ __forceinline__ uint32_t table_find(const uint2* __restrict__ pool, unsigned long long base, uint32_t lg,
                                                uint32_t w, uint32_t& slots) {
     const uint32_t mask = (1u << lg) - 1u;
+    const uint32_t* keys = reinterpret_cast<const uint32_t*>(pool + base);
+    const uint4* buckets = reinterpret_cast<const uint4*>(keys);
     uint32_t h = home_slot(w, lg);
-    const uint4* tab = reinterpret_cast<const uint4*>(pool + base);
     for (uint32_t probe = 0; probe <= mask; probe += 4u) {
-        const uint4 p0 = tab[h >> 1], p1 = tab[(h >> 1) + 1];
+        const uint4 k4 = buckets[h >> 2];
         slots = probe + 4u;
-        if (p0.x == w) return p0.y;
-        if (p0.z == w) return p0.w;
-        if (p1.x == w) return p1.y;
-        if (p1.z == w) return p1.w;
-        if (p0.x == kEmptyId || p0.z == kEmptyId || p1.x == kEmptyId || p1.z == kEmptyId) return kEmptyId;
+        int at = -1;
+        if (k4.x == w) at = 0;
+        else if (k4.y == w) at = 1;
+        else if (k4.z == w) at = 2;
+        else if (k4.w == w) at = 3;
+        if (at >= 0) return keys[(1u << lg) + h + (uint32_t)at];
+        if (k4.x == kEmptyId || k4.y == kEmptyId || k4.z == kEmptyId || k4.w == kEmptyId) return kEmptyId;
         h = (h + 4u) & mask;
     }
     return kEmptyId;
@@ -442,37 +449,6 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
 // shared-memory key queue, and then probes them with all 32 lanes.
 constexpr int kQueue = 128;
 
-// The lookup of w once its home bucket (p0, p1) has been read: the stream index if w is in the bucket,
-// kEmptyId if the bucket shows w absent, and kReadOn if the bucket is full without w.  Stream indices
-// stay below 2^32 - 2 (the host rejects longer streams), so kReadOn is never an index.
-constexpr uint32_t kReadOn = 0xFFFFFFFEu;
-
-__device__ __forceinline__ uint32_t bucket_lookup(const uint4& p0, const uint4& p1, uint32_t w) {
-    if (p0.x == w) return p0.y;
-    if (p0.z == w) return p0.w;
-    if (p1.x == w) return p1.y;
-    if (p1.z == w) return p1.w;
-    if (p0.x == kEmptyId || p0.z == kEmptyId || p1.x == kEmptyId || p1.z == kEmptyId) return kEmptyId;
-    return kReadOn;
-}
-
-// table_find from the bucket after w's home bucket (the home bucket was full without w).
-__device__ __forceinline__ uint32_t table_find_after_home(const uint2* __restrict__ pool, unsigned long long base,
-                                                          uint32_t lg, uint32_t w, uint32_t& slots) {
-    const uint32_t mask = (1u << lg) - 1u;
-    uint32_t h = (home_slot(w, lg) + 4u) & mask;
-    const uint4* tab = reinterpret_cast<const uint4*>(pool + base);
-    slots = 4u;
-    for (uint32_t probe = 4; probe <= mask; probe += 4u) {
-        const uint4 p0 = tab[h >> 1], p1 = tab[(h >> 1) + 1];
-        slots = probe + 4u;
-        const uint32_t r = bucket_lookup(p0, p1, w);
-        if (r != kReadOn) return r;
-        h = (h + 4u) & mask;
-    }
-    return kEmptyId;
-}
-
 template <bool WORK>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, unsigned long long* s_proc,
                                                uint32_t* queue, MatchQueue& mq, Work& wk) {
@@ -557,7 +533,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, unsi
 // k_insert; warps claim work dynamically, largest class first.  Dynamic shared memory: c uint64
 // counters (tau^(i) of this block).  WORK = true also tallies the table reads.
 template <bool WORK>
-__global__ void __launch_bounds__(256, 8) k_intersect(StreamDev d, BatchDev b) {
+__global__ void __launch_bounds__(256, 6) k_intersect(StreamDev d, BatchDev b) {
     extern __shared__ unsigned long long s_proc[];
     __shared__ uint32_t s_queue[256 / 32][kQueue];
     __shared__ uint32_t s_match[256 / 32][3][kMatchQ];
