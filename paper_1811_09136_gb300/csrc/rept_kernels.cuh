@@ -533,7 +533,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, unsi
 // k_insert; warps claim work dynamically, largest class first.  Dynamic shared memory: c uint64
 // counters (tau^(i) of this block).  WORK = true also tallies the table reads.
 template <bool WORK>
-__global__ void __launch_bounds__(256, 6) k_intersect(StreamDev d, BatchDev b) {
+__global__ void __launch_bounds__(256, 8) k_intersect(StreamDev d, BatchDev b) {
     extern __shared__ unsigned long long s_proc[];
     __shared__ uint32_t s_queue[256 / 32][kQueue];
     __shared__ uint32_t s_match[256 / 32][3][kMatchQ];
