@@ -474,17 +474,32 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
             n_q += __popc(m2);
         }
         __syncwarp();
-        for (uint32_t k0 = 0; k0 < n_q; k0 += 32u) {
-            bool has = false;
-            uint32_t w = 0;
-            if (k0 + lane < n_q) {
-                w = queue[k0 + lane];
-                uint32_t nslots = 0;
-                const uint32_t tl = table_find(d.pool, base_l, lg_l, w, nslots);
-                if (WORK) { ++wk.probes; wk.pslots += nslots; }
-                has = tl < x.t;
+        // two queued neighbours per lane: both home buckets are loaded before either is examined
+        const uint32_t* keys_l = reinterpret_cast<const uint32_t*>(d.pool + base_l);
+        const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
+        const uint32_t cap_l = 1u << lg_l;
+        for (uint32_t k0 = 0; k0 < n_q; k0 += 64u) {
+            const bool v1 = k0 + lane < n_q, v2 = k0 + 32u + lane < n_q;
+            const uint32_t w1 = v1 ? queue[k0 + lane] : kEmptyId, w2 = v2 ? queue[k0 + 32u + lane] : kEmptyId;
+            const uint32_t h1 = home_slot(w1, lg_l), h2 = home_slot(w2, lg_l);
+            uint4 b1 = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId), b2 = b1;
+            if (v1) b1 = buckets_l[h1 >> 2];
+            if (v2) b2 = buckets_l[h2 >> 2];
+            const int at1 = b1.x == w1 ? 0 : b1.y == w1 ? 1 : b1.z == w1 ? 2 : b1.w == w1 ? 3 : -1;
+            const int at2 = b2.x == w2 ? 0 : b2.y == w2 ? 1 : b2.z == w2 ? 2 : b2.w == w2 ? 3 : -1;
+            const bool full1 = b1.x != kEmptyId && b1.y != kEmptyId && b1.z != kEmptyId && b1.w != kEmptyId;
+            const bool full2 = b2.x != kEmptyId && b2.y != kEmptyId && b2.z != kEmptyId && b2.w != kEmptyId;
+            uint32_t r1 = kEmptyId, r2 = kEmptyId, n1 = 4u, n2 = 4u;
+            if (v1 && at1 >= 0) r1 = keys_l[cap_l + h1 + (uint32_t)at1];
+            if (v2 && at2 >= 0) r2 = keys_l[cap_l + h2 + (uint32_t)at2];
+            if (v1 && at1 < 0 && full1) r1 = table_find(d.pool, base_l, lg_l, w1, n1);  // rare: read on
+            if (v2 && at2 < 0 && full2) r2 = table_find(d.pool, base_l, lg_l, w2, n2);
+            if (WORK) {
+                if (v1) { ++wk.probes; wk.pslots += n1; }
+                if (v2) { ++wk.probes; wk.pslots += n2; }
             }
-            mq_push<WORK>(d, mq, has, x.s, x.l, w, s_proc, wk);
+            mq_push<WORK>(d, mq, v1 && r1 < x.t, x.s, x.l, w1, s_proc, wk);
+            mq_push<WORK>(d, mq, v2 && r2 < x.t, x.s, x.l, w2, s_proc, wk);
         }
         __syncwarp();
     }
