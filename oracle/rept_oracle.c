@@ -320,6 +320,8 @@ void orc_estimates(uint32_t m, uint32_t c, const uint64_t* tau_proc, const uint6
 
 typedef struct { uint32_t nbr, eidx; } fent;
 
+#define ATOMIC_INC(p) __atomic_fetch_add((p), 1ull, __ATOMIC_RELAXED)
+
 static int fent_cmp(const void* a, const void* b) {
     uint32_t x = ((const fent*)a)->nbr, y = ((const fent*)b)->nbr;
     return (x > y) - (x < y);
@@ -394,6 +396,10 @@ int orc_semitriangles(const uint32_t* src, const uint32_t* dst, uint64_t T, uint
     }
     if (rc) goto out;
 
+    /* The enumeration is split over threads by node x (OpenMP when compiled with it); counters are
+     * shared and updated atomically, so the totals do not depend on the split. */
+    uint64_t tri_count = 0;
+    #pragma omp parallel for schedule(dynamic, 64) reduction(+ : tri_count)
     for (uint32_t x = 0; x < n; ++x) {
         for (uint64_t p = off[x]; p < off[x + 1]; ++p) {
             uint32_t y = fw[p].nbr;
@@ -411,26 +417,28 @@ int orc_semitriangles(const uint32_t* src, const uint32_t* dst, uint64_t T, uint
                 int last = 0;
                 for (int q = 1; q < 3; ++q) if (e[q] > e[last]) last = q;
                 int f1 = (last + 1) % 3, f2 = (last + 2) % 3;   /* the two earliest edges */
-                if (tri_total) ++*tri_total;
-                if (tri_local) { tri_local[x]++; tri_local[y]++; tri_local[z]++; }
-                a_g[e[f1]]++; a_g[e[f2]]++;
+                ++tri_count;
+                if (tri_local) { ATOMIC_INC(&tri_local[x]); ATOMIC_INC(&tri_local[y]); ATOMIC_INC(&tri_local[z]); }
+                __atomic_fetch_add(&a_g[e[f1]], 1u, __ATOMIC_RELAXED);
+                __atomic_fetch_add(&a_g[e[f2]], 1u, __ATOMIC_RELAXED);
                 for (uint32_t k = 0; k < groups; ++k) {
                     uint32_t j1 = orc_colour(ends[f1][0], ends[f1][1], seed, k, m);
                     uint32_t j2 = orc_colour(ends[f2][0], ends[f2][1], seed, k, m);
                     uint32_t i = k * m + j1;
                     if (j1 != j2 || i >= c) continue;
-                    if (tau_proc) tau_proc[i]++;
+                    if (tau_proc) ATOMIC_INC(&tau_proc[i]);
                     uint64_t* l_sum = (i < full) ? local1 : local2;
-                    if (l_sum) { l_sum[x]++; l_sum[y]++; l_sum[z]++; }
+                    if (l_sum) { ATOMIC_INC(&l_sum[x]); ATOMIC_INC(&l_sum[y]); ATOMIC_INC(&l_sum[z]); }
                     if (tau_local_proc) {
-                        tau_local_proc[(uint64_t)i * n + x]++;
-                        tau_local_proc[(uint64_t)i * n + y]++;
-                        tau_local_proc[(uint64_t)i * n + z]++;
+                        ATOMIC_INC(&tau_local_proc[(uint64_t)i * n + x]);
+                        ATOMIC_INC(&tau_local_proc[(uint64_t)i * n + y]);
+                        ATOMIC_INC(&tau_local_proc[(uint64_t)i * n + z]);
                     }
                 }
             }
         }
     }
+    if (tri_total) *tri_total = tri_count;
     if (eta_total || eta_loc) {
         for (uint64_t t = 0; t < T; ++t) {
             uint64_t pairs = (uint64_t)a_g[t] * (a_g[t] - (a_g[t] ? 1 : 0)) / 2;

@@ -35,7 +35,7 @@ def test_mutant_is_caught(name, tmp_path):
     path = tmp_path / "rept_oracle_mutant.c"
     path.write_text(src.replace(old, new))
     lib_path = str(tmp_path / f"librept_oracle_{name}.so")
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", str(path), "-o", lib_path])
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fopenmp", "-fPIC", "-shared", str(path), "-o", lib_path])
     lib = O.load_library(lib_path)
     failed = []
     for pin in P.ALL_PINS:
