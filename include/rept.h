@@ -81,6 +81,10 @@ typedef struct rept_config {
     uint32_t flags;          /* REPT_FLAG_* */
     uint64_t expected_edges; /* sizing hint: edges the stream will carry (0: start small and grow) */
     uint64_t max_batch;      /* sizing hint: largest batch passed to an ingest call (0: 2^20) */
+    uint32_t tile_max;       /* tuning: edges whose smaller endpoint holds at most this many entries
+                                (4, 8, 16 or 32; 0: 32) share a warp with other edges, larger ones get a
+                                warp of their own; results do not depend on it */
+    uint32_t reserved;       /* must be 0 */
 } rept_config;
 
 typedef struct rept_stats {
@@ -177,6 +181,40 @@ int rept_sync(rept_state* s, void* stream);
 
 /* rept_destroy: free every allocation of the handle (NULL is a no-op).  Waits for the handle's pending work. */
 void rept_destroy(rept_state* s);
+
+/*
+ * Batched ingestion of many independent streams.  A rept_group ingests one
+ * batch into each of up to max_streams handles with one kernel launch per
+ * step of the batch path for all of them (the launch grid's y dimension
+ * ranges over the streams), instead of one launch sequence per stream.  The
+ * paper runs its processors on one stream; a group runs many streams' REPT
+ * side by side.  Counts are exactly those of calling rept_ingest_batch on
+ * each handle in turn.
+ *
+ * rept_group_create: max_streams >= 1; flags REPT_GROUP_GRAPH captures the
+ * launch sequence in a CUDA graph and replays it on later calls with the same
+ * shape (used only when no stream's pool can run out during the call).
+ */
+#define REPT_GROUP_GRAPH 1u
+typedef struct rept_group rept_group;
+int rept_group_create(uint32_t max_streams, uint32_t flags, rept_group** out);
+
+/*
+ * rept_group_ingest: append d_src[i][0..n[i]), d_dst[i][0..n[i]) to stream
+ * hs[i] for i < k (k <= max_streams; n[i] may be 0; the handles must be
+ * distinct and belong to the current device; device arrays as in
+ * rept_ingest_batch).  Enqueued on `stream`; the call synchronises once when
+ * some stream's pool might have to grow (never when every handle was created
+ * with expected_edges covering its stream, or with REPT_FLAG_FIXED_POOL).
+ * Handle flags REPT_FLAG_PROFILE and REPT_FLAG_WORK_COUNTERS are ignored here.
+ * Errors: REPT_E_INVAL (bad arguments), REPT_E_NOMEM, REPT_E_CUDA; device
+ * errors stay sticky on the handle they concern.
+ */
+int rept_group_ingest(rept_group* g, rept_state* const* hs, const uint32_t* const* d_src,
+                      const uint32_t* const* d_dst, const uint64_t* n, uint32_t k, void* stream);
+
+/* rept_group_destroy: release the group (not the handles).  NULL is a no-op. */
+void rept_group_destroy(rept_group* g);
 
 /*
  * rept_count_noalloc: count a whole edge stream in one call without

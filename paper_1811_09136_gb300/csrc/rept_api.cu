@@ -258,6 +258,10 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if (cfg->m == 0 || cfg->c == 0 || cfg->n_nodes == 0 || cfg->n_nodes == 0xFFFFFFFFu) return REPT_E_INVAL;
     if (cfg->c > cfg->m && cfg->c % cfg->m != 0) return REPT_E_INVAL;
     if (cfg->c > kMaxProcessors) return REPT_E_INVAL;
+    if (cfg->tile_max != 0 && cfg->tile_max != 4 && cfg->tile_max != 8 && cfg->tile_max != 16 &&
+        cfg->tile_max != 32)
+        return REPT_E_INVAL;
+    if (cfg->reserved != 0) return REPT_E_INVAL;
     cudaStream_t st = as_stream(stream);
     rept_state* s = new (std::nothrow) rept_state();
     if (!s) return REPT_E_NOMEM;
@@ -285,6 +289,7 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     d.n_nodes = n;
     d.seed = cfg->seed;
     d.fm = make_fastmod(cfg->m);
+    d.tile_max = cfg->tile_max == 0 ? 32u : cfg->tile_max;
     const unsigned long long mb = cfg->max_batch ? cfg->max_batch : (1ull << 20);
     unsigned long long quads = cfg->expected_edges ? quads_bound(cfg->expected_edges) : quads_bound(mb);
     if (quads > 0xFFFFFFFFull) quads = 0xFFFFFFFFull;
@@ -494,6 +499,234 @@ void rept_destroy(rept_state* s) {
     if (s->h_ctrl) cudaFreeHost(s->h_ctrl);
     if (s->h_global) cudaFreeHost(s->h_global);
     delete s;
+}
+
+}  // extern "C"
+
+namespace rept {
+namespace {
+
+// Pool requests of k streams after k_plan: {pool_top, need_quads, status} per stream.
+__global__ void k_gather_requests(const StreamDev* __restrict__ ds, uint32_t k, unsigned long long* out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) {
+        const Ctrl* c = ds[i].ctrl;
+        out[3 * i] = c->pool_top;
+        out[3 * i + 1] = c->need_quads;
+        out[3 * i + 2] = c->status;
+    }
+}
+
+}  // namespace
+}  // namespace rept
+
+struct rept_group {
+    uint32_t max_streams = 0, flags = 0;
+    int sm_count = 0, intersect_per_sm = 1;
+    StreamDev* d_sd = nullptr;  // device descriptor arrays read by the _multi kernels
+    BatchDev* d_bd = nullptr;
+    unsigned long long* d_req = nullptr;
+    // two pinned staging slots, so that a replayed graph's descriptor copy never races the host
+    StreamDev* h_sd[2] = {nullptr, nullptr};
+    BatchDev* h_bd[2] = {nullptr, nullptr};
+    unsigned long long* h_req = nullptr;
+    cudaEvent_t slot_done[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    unsigned long long shape[2][6] = {{0}};  // what each slot's graph was captured for
+    int slot = 0;
+};
+
+namespace {
+
+struct GroupShape {
+    uint32_t k;
+    int x_edge, x_big, x_huge, x_int;
+    size_t smem;
+};
+
+// Enqueue the batch path for all k streams: one launch per step.  With `split`, stop after
+// k_plan (the caller reads the pool requests, grows pools, and calls again with split = 2).
+int enqueue_group(rept_group* g, const GroupShape& sh, cudaStream_t st, int part) {
+    const dim3 blk(256);
+    const uint32_t k = sh.k;
+    if (part != 2) {
+        k_classify_multi<<<dim3(sh.x_edge, k), blk, 0, st>>>(g->d_sd, g->d_bd);
+        k_plan_multi<<<dim3(sh.x_edge, k), blk, 0, st>>>(g->d_sd, g->d_bd);
+    }
+    if (part != 1) {
+        k_commit_multi<<<dim3(sh.x_edge, k), blk, 0, st>>>(g->d_sd, g->d_bd);
+        k_rehash_big_multi<<<dim3(sh.x_big, k), blk, 0, st>>>(g->d_sd, g->d_bd);
+        k_rehash_huge_multi<<<dim3(sh.x_huge, k), dim3(1024), 0, st>>>(g->d_sd, g->d_bd);
+        k_insert_multi<<<dim3(sh.x_edge, k), blk, 0, st>>>(g->d_sd, g->d_bd);
+        k_sort_scan_multi<<<dim3(1, k), dim3(1024), 0, st>>>(g->d_sd, g->d_bd);
+        k_sort_scatter_multi<<<dim3(sh.x_edge, k), blk, 0, st>>>(g->d_sd, g->d_bd);
+        k_intersect_multi<false><<<dim3(sh.x_int, k), blk, sh.smem, st>>>(g->d_sd, g->d_bd);
+    }
+    const int launched = part == 1 ? 2 : (part == 2 ? 7 : 9);
+    g_launches.fetch_add((unsigned long long)launched, std::memory_order_relaxed);
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        (void)cudaGetLastError();
+        return REPT_E_CUDA;
+    }
+    return REPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rept_group_create(uint32_t max_streams, uint32_t flags, rept_group** out) {
+    if (!out || max_streams == 0 || max_streams > 65535u) return REPT_E_INVAL;
+    *out = nullptr;
+    rept_group* g = new (std::nothrow) rept_group();
+    if (!g) return REPT_E_NOMEM;
+    g->max_streams = max_streams;
+    g->flags = flags;
+    auto fail = [&](int code) {
+        rept_group_destroy(g);
+        return code;
+    };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(REPT_E_CUDA);
+    if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fail(REPT_E_CUDA);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_intersect_multi<false>, 256,
+                                                      kMaxProcessors * sizeof(unsigned long long) / 8) !=
+        cudaSuccess)
+        return fail(REPT_E_CUDA);
+    g->intersect_per_sm = std::max(per_sm, 1);
+    if (cudaMalloc(&g->d_sd, max_streams * sizeof(StreamDev)) != cudaSuccess) return fail(REPT_E_NOMEM);
+    if (cudaMalloc(&g->d_bd, max_streams * sizeof(BatchDev)) != cudaSuccess) return fail(REPT_E_NOMEM);
+    if (cudaMalloc(&g->d_req, 3ull * max_streams * sizeof(unsigned long long)) != cudaSuccess)
+        return fail(REPT_E_NOMEM);
+    for (int i = 0; i < 2; ++i) {
+        if (cudaMallocHost(&g->h_sd[i], max_streams * sizeof(StreamDev)) != cudaSuccess) return fail(REPT_E_NOMEM);
+        if (cudaMallocHost(&g->h_bd[i], max_streams * sizeof(BatchDev)) != cudaSuccess) return fail(REPT_E_NOMEM);
+        if (cudaEventCreateWithFlags(&g->slot_done[i], cudaEventDisableTiming) != cudaSuccess)
+            return fail(REPT_E_CUDA);
+    }
+    if (cudaMallocHost(&g->h_req, 3ull * max_streams * sizeof(unsigned long long)) != cudaSuccess)
+        return fail(REPT_E_NOMEM);
+    *out = g;
+    return REPT_OK;
+}
+
+void rept_group_destroy(rept_group* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 2; ++i) {
+        if (g->exec[i]) cudaGraphExecDestroy(g->exec[i]);
+        if (g->slot_done[i]) cudaEventDestroy(g->slot_done[i]);
+        if (g->h_sd[i]) cudaFreeHost(g->h_sd[i]);
+        if (g->h_bd[i]) cudaFreeHost(g->h_bd[i]);
+    }
+    if (g->h_req) cudaFreeHost(g->h_req);
+    cudaFree(g->d_sd);
+    cudaFree(g->d_bd);
+    cudaFree(g->d_req);
+    delete g;
+}
+
+int rept_group_ingest(rept_group* g, rept_state* const* hs, const uint32_t* const* d_src,
+                      const uint32_t* const* d_dst, const uint64_t* n, uint32_t k, void* stream) {
+    if (!g || !hs || !d_src || !d_dst || !n || k == 0 || k > g->max_streams) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    unsigned long long max_n = 0;
+    uint32_t max_c = 1;
+    bool guaranteed = true;
+    for (uint32_t i = 0; i < k; ++i) {
+        rept_state* s = hs[i];
+        if (!s) return REPT_E_INVAL;
+        if (n[i] && (!d_src[i] || !d_dst[i])) return REPT_E_INVAL;
+        if (s->next_t + n[i] >= 0xFFFFFFFEull) return REPT_E_INVAL;
+        int rc = ensure_batch_scratch(s, std::max<unsigned long long>(n[i], 1ull), st);
+        if (rc) return rc;
+        max_n = std::max<unsigned long long>(max_n, n[i]);
+        max_c = std::max(max_c, s->cfg.c);
+        const bool fixed = (s->cfg.flags & REPT_FLAG_FIXED_POOL) != 0;
+        if (!fixed && s->d.pool_quads < quads_bound(s->next_t + n[i])) guaranteed = false;
+    }
+    // launch shape: the edge kernels cover the largest batch, the rest share the SMs between streams
+    GroupShape sh{};
+    sh.k = k;
+    const unsigned long long pow2 = max_n <= 256 ? 256ull : (1ull << (64 - __builtin_clzll(max_n - 1)));
+    const int per_stream_cap = std::max(2, (8 * g->sm_count + (int)k - 1) / (int)k);
+    sh.x_edge = (int)std::min<unsigned long long>((pow2 + 255) / 256, (unsigned long long)per_stream_cap);
+    sh.x_big = std::max(1, 4 * g->sm_count / (int)k);
+    sh.x_huge = std::max(1, 2 * g->sm_count / (int)k);
+    sh.x_int = std::max(1, g->intersect_per_sm * g->sm_count / (int)k);
+    sh.smem = (size_t)max_c * sizeof(unsigned long long);
+
+    const int slot = g->slot;
+    g->slot ^= 1;
+    if (cudaEventSynchronize(g->slot_done[slot]) != cudaSuccess) return REPT_E_CUDA;  // slot free again
+    StreamDev* hsd = g->h_sd[slot];
+    BatchDev* hbd = g->h_bd[slot];
+    for (uint32_t i = 0; i < k; ++i) {
+        hsd[i] = hs[i]->d;
+        hbd[i] = BatchDev{d_src[i], d_dst[i], n[i], hs[i]->next_t};
+    }
+    auto upload = [&]() -> int {
+        REPT_CUDA(cudaMemcpyAsync(g->d_sd, hsd, k * sizeof(StreamDev), cudaMemcpyHostToDevice, st));
+        REPT_CUDA(cudaMemcpyAsync(g->d_bd, hbd, k * sizeof(BatchDev), cudaMemcpyHostToDevice, st));
+        return REPT_OK;
+    };
+    int rc = REPT_OK;
+    if (!guaranteed) {
+        // classify + plan, read every stream's pool request, grow the pools that need it, go on
+        if ((rc = upload())) return rc;
+        if ((rc = enqueue_group(g, sh, st, 1))) return rc;
+        k_gather_requests<<<(k + 255) / 256, 256, 0, st>>>(g->d_sd, k, g->d_req);
+        REPT_CUDA(cudaMemcpyAsync(g->h_req, g->d_req, 3ull * k * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                  st));
+        REPT_CUDA(cudaStreamSynchronize(st));
+        bool grew = false;
+        for (uint32_t i = 0; i < k; ++i) {
+            rept_state* s = hs[i];
+            const unsigned long long top = g->h_req[3 * i], need = g->h_req[3 * i + 1];
+            const bool fixed = (s->cfg.flags & REPT_FLAG_FIXED_POOL) != 0;
+            if (!fixed && g->h_req[3 * i + 2] == 0 && top + need > s->d.pool_quads) {
+                s->h_ctrl->pool_top = top;
+                if ((rc = grow_pool(s, top + need + (top + need) / 2 + 1024, st))) return rc;
+                hsd[i] = s->d;
+                grew = true;
+            }
+        }
+        if (grew) REPT_CUDA(cudaMemcpyAsync(g->d_sd, hsd, k * sizeof(StreamDev), cudaMemcpyHostToDevice, st));
+        if ((rc = enqueue_group(g, sh, st, 2))) return rc;
+    } else if (g->flags & REPT_GROUP_GRAPH) {
+        const unsigned long long key[6] = {k, (unsigned long long)sh.x_edge, (unsigned long long)sh.x_big,
+                                           (unsigned long long)sh.x_huge, (unsigned long long)sh.x_int, sh.smem};
+        bool same = g->exec[slot] != nullptr;
+        for (int j = 0; j < 6 && same; ++j) same = g->shape[slot][j] == key[j];
+        if (!same) {
+            if (g->exec[slot]) {
+                cudaGraphExecDestroy(g->exec[slot]);
+                g->exec[slot] = nullptr;
+            }
+            cudaGraph_t graph = nullptr;
+            REPT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            int rc_cap = upload();
+            if (!rc_cap) rc_cap = enqueue_group(g, sh, st, 0);
+            const cudaError_t e_end = cudaStreamEndCapture(st, &graph);
+            if (rc_cap) return rc_cap;
+            if (e_end != cudaSuccess) return REPT_E_CUDA;
+            const cudaError_t e_inst = cudaGraphInstantiate(&g->exec[slot], graph, 0);
+            cudaGraphDestroy(graph);
+            if (e_inst != cudaSuccess) return REPT_E_CUDA;
+            for (int j = 0; j < 6; ++j) g->shape[slot][j] = key[j];
+            g_launches.fetch_sub(9, std::memory_order_relaxed);  // captured, not launched
+        }
+        REPT_CUDA(cudaGraphLaunch(g->exec[slot], st));
+        g_launches.fetch_add(9, std::memory_order_relaxed);
+    } else {
+        if ((rc = upload())) return rc;
+        if ((rc = enqueue_group(g, sh, st, 0))) return rc;
+    }
+    REPT_CUDA(cudaEventRecord(g->slot_done[slot], st));
+    for (uint32_t i = 0; i < k; ++i) hs[i]->next_t += n[i];
+    return REPT_OK;
 }
 
 const char* rept_strerror(int code) {

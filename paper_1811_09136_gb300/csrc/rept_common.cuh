@@ -118,7 +118,8 @@ struct __align__(16) WorkItem {
 struct StreamDev {
     uint32_t m, c, groups, n_nodes;
     uint64_t seed;
-    FastMod fm;  // x mod m
+    FastMod fm;         // x mod m
+    uint32_t tile_max;  // edges whose smaller endpoint has more entries get a warp (4, 8, 16 or 32)
     uint2* meta;
     uint2* pool;
     unsigned long long pool_quads;
@@ -188,9 +189,11 @@ __host__ __device__ __forceinline__ uint32_t list_slots(uint32_t lg) { return lg
 __host__ __device__ __forceinline__ uint32_t block_quads(uint32_t lg) { return ((1u << lg) + list_slots(lg)) >> 2; }
 
 // k_intersect work class of an edge whose smaller endpoint holds cnt entries: tiles of 4, 8, 16, 32
-// lanes (one entry per lane), then a warp per edge for up to 256 entries and for more.
-__host__ __device__ __forceinline__ int bin_of_cnt(uint32_t cnt) {
-    return cnt <= 4u ? 0 : cnt <= 8u ? 1 : cnt <= 16u ? 2 : cnt <= 32u ? 3 : cnt <= 256u ? 4 : 5;
+// lanes (one entry per lane) up to tile_max entries, then a warp per edge for up to 256 entries and
+// for more.
+__host__ __device__ __forceinline__ int bin_of_cnt(uint32_t cnt, uint32_t tile_max) {
+    if (cnt > tile_max) return cnt <= 256u ? 4 : 5;
+    return cnt <= 4u ? 0 : cnt <= 8u ? 1 : cnt <= 16u ? 2 : 3;
 }
 
 // Home slot of neighbour w in a table of 2^lg slots: the first slot of a 4-slot (32-byte) bucket

@@ -41,7 +41,7 @@ __device__ __forceinline__ bool table_insert(uint2* pool, unsigned long long bas
     return false;
 }
 
-__global__ void k_classify(StreamDev d, BatchDev b) {
+__device__ __forceinline__ void k_classify_body(const StreamDev& d, const BatchDev& b) {
     // the previous batch's work list is consumed: clear the counting-sort histogram
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < kSortBuckets; i += gridDim.x * blockDim.x)
         d.hist[i] = 0u;
@@ -69,7 +69,7 @@ __global__ void k_classify(StreamDev d, BatchDev b) {
     }
 }
 
-__global__ void k_plan(StreamDev d) {
+__device__ __forceinline__ void k_plan_body(const StreamDev& d) {
     if (d.ctrl->status) return;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long n_t = d.ctrl->n_touched;
@@ -109,7 +109,7 @@ __device__ __forceinline__ bool move_block(uint2* pool, uint32_t old_off, uint32
 // One thread per touched node; a block holding more than 8 entries is left to k_rehash_big (a warp
 // each) or k_rehash_huge (a thread block each).  add[x] keeps the batch's new-entry count for
 // k_insert, which counts it back down to zero; a batch that is not applied clears it here.
-__global__ void k_commit(StreamDev d) {
+__device__ __forceinline__ void k_commit_body(const StreamDev& d) {
     const unsigned status = d.ctrl->status;
     const unsigned long long n_t = d.ctrl->n_touched;
     const unsigned long long need = d.ctrl->need_quads, top = d.ctrl->pool_top;
@@ -150,7 +150,7 @@ __global__ void k_commit(StreamDev d) {
 }
 
 // Move the blocks of 9..2048 entries listed by k_commit: one warp per node.
-__global__ void k_rehash_big(StreamDev d) {
+__device__ __forceinline__ void k_rehash_big_body(const StreamDev& d) {
     const unsigned long long n_big = d.ctrl->n_big, top = d.ctrl->pool_top;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -169,7 +169,7 @@ __global__ void k_rehash_big(StreamDev d) {
 }
 
 // Move the blocks of more than 2048 entries listed by k_commit: thread blocks claim one node at a time.
-__global__ void __launch_bounds__(1024) k_rehash_huge(StreamDev d) {
+__device__ __forceinline__ void k_rehash_huge_body(const StreamDev& d) {
     __shared__ unsigned long long s_k;
     __shared__ int s_bad;
     const unsigned long long n_huge = d.ctrl->n_huge, top = d.ctrl->pool_top;
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(1024) k_rehash_huge(StreamDev d) {
     }
 }
 
-__global__ void k_insert(StreamDev d, BatchDev b) {
+__device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev& b) {
     Ctrl* ct = d.ctrl;
     const unsigned status = ct->status;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -245,7 +245,7 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
                 it.t = (uint32_t)(b.t0 + e);
                 it.lgs = table_lg(ms.y) | (table_lg(ml.y) << 8);
                 it.cnt_s = ms.y;
-                key = (uint32_t)bin_of_cnt(ms.y) * kKeyBuckets + ((it.l * 0x9E3779B1u) >> (32 - kKeyBits));
+                key = (uint32_t)bin_of_cnt(ms.y, d.tile_max) * kKeyBuckets + ((it.l * 0x9E3779B1u) >> (32 - kKeyBits));
             }
         }
         it.key = key;
@@ -262,7 +262,7 @@ __global__ void k_insert(StreamDev d, BatchDev b) {
 
 // Exclusive scan of the counting-sort histogram (one block of 1024 threads): counts become the
 // first position of each key, and the class boundaries are recorded.
-__global__ void __launch_bounds__(1024) k_sort_scan(StreamDev d) {
+__device__ __forceinline__ void k_sort_scan_body(const StreamDev& d) {
     constexpr uint32_t kPer = kSortBuckets / 1024;
     __shared__ uint32_t warp_sum[32];
     if (d.ctrl->status) return;
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(1024) k_sort_scan(StreamDev d) {
 }
 
 // Scatter each edge that can close a wedge to its place in the sorted work list.
-__global__ void k_sort_scatter(StreamDev d, BatchDev b) {
+__device__ __forceinline__ void k_sort_scatter_body(const StreamDev& d, const BatchDev& b) {
     if (d.ctrl->status) return;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -548,7 +548,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, unsi
 // k_insert; warps claim work dynamically, largest class first.  Dynamic shared memory: c uint64
 // counters (tau^(i) of this block).  WORK = true also tallies the table reads.
 template <bool WORK>
-__global__ void __launch_bounds__(256, 8) k_intersect(StreamDev d, BatchDev b) {
+__device__ __forceinline__ void k_intersect_body(const StreamDev& d, const BatchDev& b) {
     extern __shared__ unsigned long long s_proc[];
     __shared__ uint32_t s_queue[256 / 32][kQueue];
     __shared__ uint32_t s_match[256 / 32][3][kMatchQ];
@@ -589,6 +589,114 @@ __global__ void __launch_bounds__(256, 8) k_intersect(StreamDev d, BatchDev b) {
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < d.c; i += blockDim.x)
         if (s_proc[i]) atomicAdd(&d.proc[i], s_proc[i]);
+}
+
+// Kernel entry points.  Each batch kernel exists twice: for one stream (state and batch passed by
+// value) and for many streams at once (`_multi`: blockIdx.y selects the stream, whose state and batch
+// descriptors are read from device arrays; blockIdx.x / gridDim.x then range over that stream's blocks).
+__global__ void k_classify(StreamDev d, BatchDev b) { k_classify_body(d, b); }
+
+__global__ void k_classify_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
+    __shared__ StreamDev sd;
+    __shared__ BatchDev sb;
+    if (threadIdx.x == 0) {
+        sd = ds[blockIdx.y];
+        sb = bs[blockIdx.y];
+    }
+    __syncthreads();
+    k_classify_body(sd, sb);
+}
+
+__global__ void k_plan(StreamDev d) { k_plan_body(d); }
+
+__global__ void k_plan_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
+    (void)bs;
+    __shared__ StreamDev sd;
+    if (threadIdx.x == 0) sd = ds[blockIdx.y];
+    __syncthreads();
+    k_plan_body(sd);
+}
+
+__global__ void k_commit(StreamDev d) { k_commit_body(d); }
+
+__global__ void k_commit_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
+    (void)bs;
+    __shared__ StreamDev sd;
+    if (threadIdx.x == 0) sd = ds[blockIdx.y];
+    __syncthreads();
+    k_commit_body(sd);
+}
+
+__global__ void k_rehash_big(StreamDev d) { k_rehash_big_body(d); }
+
+__global__ void k_rehash_big_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
+    (void)bs;
+    __shared__ StreamDev sd;
+    if (threadIdx.x == 0) sd = ds[blockIdx.y];
+    __syncthreads();
+    k_rehash_big_body(sd);
+}
+
+__global__ void __launch_bounds__(1024) k_rehash_huge(StreamDev d) { k_rehash_huge_body(d); }
+
+__global__ void __launch_bounds__(1024) k_rehash_huge_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
+    (void)bs;
+    __shared__ StreamDev sd;
+    if (threadIdx.x == 0) sd = ds[blockIdx.y];
+    __syncthreads();
+    k_rehash_huge_body(sd);
+}
+
+__global__ void k_insert(StreamDev d, BatchDev b) { k_insert_body(d, b); }
+
+__global__ void k_insert_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
+    __shared__ StreamDev sd;
+    __shared__ BatchDev sb;
+    if (threadIdx.x == 0) {
+        sd = ds[blockIdx.y];
+        sb = bs[blockIdx.y];
+    }
+    __syncthreads();
+    k_insert_body(sd, sb);
+}
+
+__global__ void __launch_bounds__(1024) k_sort_scan(StreamDev d) { k_sort_scan_body(d); }
+
+__global__ void __launch_bounds__(1024) k_sort_scan_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
+    (void)bs;
+    __shared__ StreamDev sd;
+    if (threadIdx.x == 0) sd = ds[blockIdx.y];
+    __syncthreads();
+    k_sort_scan_body(sd);
+}
+
+__global__ void k_sort_scatter(StreamDev d, BatchDev b) { k_sort_scatter_body(d, b); }
+
+__global__ void k_sort_scatter_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
+    __shared__ StreamDev sd;
+    __shared__ BatchDev sb;
+    if (threadIdx.x == 0) {
+        sd = ds[blockIdx.y];
+        sb = bs[blockIdx.y];
+    }
+    __syncthreads();
+    k_sort_scatter_body(sd, sb);
+}
+
+template <bool WORK>
+__global__ void __launch_bounds__(256, 8) k_intersect(StreamDev d, BatchDev b) { k_intersect_body<WORK>(d, b); }
+
+template <bool WORK>
+__global__ void __launch_bounds__(256, 8) k_intersect_multi(const StreamDev* __restrict__ ds,
+                                                             const BatchDev* __restrict__ bs) {
+    __shared__ StreamDev sd;
+    __shared__ BatchDev sb;
+    if (threadIdx.x == 0) {
+        sd = ds[blockIdx.y];
+        sb = bs[blockIdx.y];
+    }
+    __syncthreads();
+    k_intersect_body<WORK>(sd, sb);
 }
 
 // tau_hat_v = f * sum_i tau_v^(i), f formed in double on the host.

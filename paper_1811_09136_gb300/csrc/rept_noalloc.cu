@@ -98,6 +98,7 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
     d.n_nodes = n_nodes;
     d.seed = seed;
     d.fm = make_fastmod(m);
+    d.tile_max = 32u;
     d.meta = reinterpret_cast<uint2*>(sc + L.meta);
     d.add = reinterpret_cast<uint32_t*>(sc + L.add);
     d.touched = reinterpret_cast<uint32_t*>(sc + L.touched);

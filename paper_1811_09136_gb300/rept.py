@@ -34,7 +34,7 @@ class ReptError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("m", ctypes.c_uint32), ("c", ctypes.c_uint32), ("seed", ctypes.c_uint64),
                 ("n_nodes", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("expected_edges", ctypes.c_uint64),
-                ("max_batch", ctypes.c_uint64)]
+                ("max_batch", ctypes.c_uint64), ("tile_max", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -129,13 +129,13 @@ class ReptStream:
     """One edge stream counted by REPT on the current CUDA device (see include/rept.h)."""
 
     def __init__(self, n_nodes: int, m: int, c: int, seed: int = 1, expected_edges: int = 0,
-                 max_batch: int = 1 << 20, flags: int = 0, stream=None):
+                 max_batch: int = 1 << 20, flags: int = 0, stream=None, tile_max: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ReptStream needs a CUDA device; there is no CPU fallback")
         lib = load()
         self.n_nodes, self.m, self.c, self.seed = int(n_nodes), int(m), int(c), int(seed)
-        cfg = Config(self.m, self.c, self.seed, self.n_nodes, flags, expected_edges, max_batch)
+        cfg = Config(self.m, self.c, self.seed, self.n_nodes, flags, expected_edges, max_batch, tile_max, 0)
         h = ctypes.c_void_p()
         _check(lib.rept_create(ctypes.byref(cfg), _cur_stream(stream), ctypes.byref(h)), "rept_create")
         self._h = h

@@ -1,0 +1,70 @@
+"""The batched path: many streams through one rept_group give every stream exactly the counts of
+the plain single-stream path and of the oracle.  Plus host-side checks of the stream mix."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1811_09136_gb300 import batched
+
+
+def test_mix_is_deterministic_and_in_range():
+    a = batched.mix_specs(256, seed=1000)
+    b = batched.mix_specs(256, seed=1000)
+    assert [(x.kind, x.n_nodes, x.m) for x in a] == [(x.kind, x.n_nodes, x.m) for x in b]
+    assert all(1e4 <= x.n_nodes <= 2e6 for x in a)
+    assert all(10 <= x.edges_per_node <= 40 for x in a)
+    assert all(2.1 <= x.gamma <= 2.5 for x in a)
+    assert {x.m for x in a} == {10, 20, 100}
+    kinds = sum(x.kind == "rmat" for x in a)
+    assert 90 < kinds < 166                      # both graph families, about half each
+    logn = np.log([x.n_nodes for x in a])
+    assert abs(logn.mean() - 0.5 * (math.log(1e4) + math.log(2e6))) < 0.5  # log-uniform centre
+
+
+def test_waves_respect_the_budget():
+    from paper_1811_09136_gb300.graphgen import EdgeStream
+    streams = [EdgeStream(np.zeros(n, np.uint32), np.zeros(n, np.uint32), 1000) for n in (10, 5000, 20, 70000, 3)]
+    budget = batched._state_bytes(1000, 70000, 64) + 8 * 70000 + 10
+    waves = list(batched._waves(streams, 64, budget))
+    assert sorted(i for w in waves for i in w) == list(range(5))
+    for w in waves:
+        used = sum(batched._state_bytes(1000, len(streams[i]), min(64, len(streams[i]))) + 8 * len(streams[i])
+                   for i in w)
+        assert used <= budget or len(w) == 1
+
+
+def _mix(k=7, seed=31):
+    specs = batched.mix_specs(k, seed=seed, n_min=800, n_max=12_000, epn=(4.0, 12.0))
+    streams = batched.generate_all(specs, processes=1)
+    params = [(sp.m, sp.m, sp.hash_seed) for sp in specs]
+    return streams, params
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("graph,presize,batch", [(True, True, 1 << 12), (False, True, 777), (True, False, 1 << 10)])
+def test_batched_equals_plain_and_oracle(graph, presize, batch):
+    streams, params = _mix()
+    res_b, _ = batched.run_batched(streams, params, batch=batch, graph=graph, presize=presize,
+                                   local_estimates=True)
+    res_p, _ = batched.run_plain(streams, params, batch=batch, local_estimates=True)
+    for s, (m, c, seed), rb, rp in zip(streams, params, res_b, res_p):
+        ref = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, seed, pair_counters=False)
+        ref_g, ref_loc = O.estimates(m, c, ref, s.n_nodes)
+        for r in (rb, rp):
+            assert np.array_equal(r.proc, ref.tau_proc)
+            assert np.array_equal(r.local, ref.local1)
+            assert abs(r.tau_hat - ref_g) <= 1e-12 * max(abs(ref_g), 1.0)
+            np.testing.assert_allclose(r.local_hat, ref_loc, rtol=1e-12, atol=0)
+
+
+@pytest.mark.gpu
+def test_batched_small_memory_budget_runs_in_waves():
+    streams, params = _mix(5, seed=44)
+    budget = max(batched._state_bytes(s.n_nodes, len(s), 1 << 11) + 8 * len(s) for s in streams) + 1
+    assert len(list(batched._waves(streams, 1 << 11, budget))) > 1
+    res_b, _ = batched.run_batched(streams, params, batch=1 << 11, budget=budget)
+    for s, (m, c, seed), rb in zip(streams, params, res_b):
+        ref = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, seed, pair_counters=False)
+        assert np.array_equal(rb.proc, ref.tau_proc) and np.array_equal(rb.local, ref.local1)
