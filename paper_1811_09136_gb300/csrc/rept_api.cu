@@ -534,6 +534,7 @@ struct rept_group {
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     unsigned long long shape[2][6] = {{0}};  // what each slot's graph was captured for
     int slot = 0;
+    cudaStream_t capture = nullptr;  // private stream the graphs are captured on (the legacy stream cannot be)
 };
 
 namespace {
@@ -608,6 +609,8 @@ int rept_group_create(uint32_t max_streams, uint32_t flags, rept_group** out) {
     }
     if (cudaMallocHost(&g->h_req, 3ull * max_streams * sizeof(unsigned long long)) != cudaSuccess)
         return fail(REPT_E_NOMEM);
+    if ((flags & REPT_GROUP_GRAPH) && cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(REPT_E_CUDA);
     *out = g;
     return REPT_OK;
 }
@@ -622,6 +625,7 @@ void rept_group_destroy(rept_group* g) {
         if (g->h_bd[i]) cudaFreeHost(g->h_bd[i]);
     }
     if (g->h_req) cudaFreeHost(g->h_req);
+    if (g->capture) cudaStreamDestroy(g->capture);
     cudaFree(g->d_sd);
     cudaFree(g->d_bd);
     cudaFree(g->d_req);
@@ -705,11 +709,16 @@ int rept_group_ingest(rept_group* g, rept_state* const* hs, const uint32_t* cons
                 cudaGraphExecDestroy(g->exec[slot]);
                 g->exec[slot] = nullptr;
             }
+            // capture on the private stream (nothing runs), replay on the caller's
             cudaGraph_t graph = nullptr;
-            REPT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            int rc_cap = upload();
-            if (!rc_cap) rc_cap = enqueue_group(g, sh, st, 0);
-            const cudaError_t e_end = cudaStreamEndCapture(st, &graph);
+            cudaStream_t cs = g->capture;
+            REPT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            int rc_cap = REPT_OK;
+            if (cudaMemcpyAsync(g->d_sd, hsd, k * sizeof(StreamDev), cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+                cudaMemcpyAsync(g->d_bd, hbd, k * sizeof(BatchDev), cudaMemcpyHostToDevice, cs) != cudaSuccess)
+                rc_cap = REPT_E_CUDA;
+            if (!rc_cap) rc_cap = enqueue_group(g, sh, cs, 0);
+            const cudaError_t e_end = cudaStreamEndCapture(cs, &graph);
             if (rc_cap) return rc_cap;
             if (e_end != cudaSuccess) return REPT_E_CUDA;
             const cudaError_t e_inst = cudaGraphInstantiate(&g->exec[slot], graph, 0);
