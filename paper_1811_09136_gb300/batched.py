@@ -205,14 +205,14 @@ def run_batched(streams, params, batch: int = 1 << 18, tile_max: int = 32, graph
             srcs.append(torch.from_numpy(s.src.view(np.int32)).cuda())
             dsts.append(torch.from_numpy(s.dst.view(np.int32)).cuda())
         group = ReptGroup(len(wave), graph=graph)
-        empty = torch.empty(0, dtype=torch.int32, device="cuda")
         rounds = max((len(streams[i]) + batch - 1) // batch for i in wave)
         torch.cuda.synchronize()
         t = time.perf_counter()
         for r in range(rounds):
-            a = [x[r * batch:(r + 1) * batch] if r * batch < x.numel() else empty for x in srcs]
-            b = [x[r * batch:(r + 1) * batch] if r * batch < x.numel() else empty for x in dsts]
-            group.ingest(handles, a, b)
+            # only the streams that still have edges take part, so the finished ones free their SMs
+            live = [j for j, x in enumerate(srcs) if r * batch < x.numel()]
+            group.ingest([handles[j] for j in live], [srcs[j][r * batch:(r + 1) * batch] for j in live],
+                         [dsts[j][r * batch:(r + 1) * batch] for j in live])
         for h in handles:
             h.sync()
         torch.cuda.synchronize()
