@@ -526,6 +526,8 @@ struct rept_group {
     StreamDev* d_sd = nullptr;  // device descriptor arrays read by the _multi kernels
     BatchDev* d_bd = nullptr;
     unsigned long long* d_req = nullptr;
+    unsigned long long* d_pref = nullptr;    // [kBins * (max_streams + 1)] item prefixes (k_group_prefix)
+    unsigned long long* d_cursor = nullptr;  // [kBins] claim cursors of k_intersect_group
     // two pinned staging slots, so that a replayed graph's descriptor copy never races the host
     StreamDev* h_sd[2] = {nullptr, nullptr};
     BatchDev* h_bd[2] = {nullptr, nullptr};
@@ -561,9 +563,11 @@ int enqueue_group(rept_group* g, const GroupShape& sh, cudaStream_t st, int part
         k_insert_multi<<<dim3(sh.x_edge, k), blk, 0, st>>>(g->d_sd, g->d_bd);
         k_sort_scan_multi<<<dim3(1, k), dim3(1024), 0, st>>>(g->d_sd, g->d_bd);
         k_sort_scatter_multi<<<dim3(sh.x_edge, k), blk, 0, st>>>(g->d_sd, g->d_bd);
-        k_intersect_multi<false><<<dim3(sh.x_int, k), blk, sh.smem, st>>>(g->d_sd, g->d_bd);
+        // one grid for all streams' intersection work
+        k_group_prefix<<<1, 1024, 0, st>>>(g->d_sd, k, g->d_pref, g->d_cursor);
+        k_intersect_group<<<g->intersect_per_sm * g->sm_count, blk, 0, st>>>(g->d_sd, k, g->d_pref, g->d_cursor);
     }
-    const int launched = part == 1 ? 2 : (part == 2 ? 7 : 9);
+    const int launched = part == 1 ? 2 : (part == 2 ? 8 : 10);
     g_launches.fetch_add((unsigned long long)launched, std::memory_order_relaxed);
     if (cudaPeekAtLastError() != cudaSuccess) {
         (void)cudaGetLastError();
@@ -592,15 +596,17 @@ int rept_group_create(uint32_t max_streams, uint32_t flags, rept_group** out) {
     if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return fail(REPT_E_CUDA);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_intersect_multi<false>, 256,
-                                                      kMaxProcessors * sizeof(unsigned long long) / 8) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_intersect_group, 256, 0) != cudaSuccess)
         return fail(REPT_E_CUDA);
     g->intersect_per_sm = std::max(per_sm, 1);
     if (cudaMalloc(&g->d_sd, max_streams * sizeof(StreamDev)) != cudaSuccess) return fail(REPT_E_NOMEM);
     if (cudaMalloc(&g->d_bd, max_streams * sizeof(BatchDev)) != cudaSuccess) return fail(REPT_E_NOMEM);
     if (cudaMalloc(&g->d_req, 3ull * max_streams * sizeof(unsigned long long)) != cudaSuccess)
         return fail(REPT_E_NOMEM);
+    if (cudaMalloc(&g->d_pref, (unsigned long long)kBins * (max_streams + 1) * sizeof(unsigned long long)) !=
+        cudaSuccess)
+        return fail(REPT_E_NOMEM);
+    if (cudaMalloc(&g->d_cursor, kBins * sizeof(unsigned long long)) != cudaSuccess) return fail(REPT_E_NOMEM);
     for (int i = 0; i < 2; ++i) {
         if (cudaMallocHost(&g->h_sd[i], max_streams * sizeof(StreamDev)) != cudaSuccess) return fail(REPT_E_NOMEM);
         if (cudaMallocHost(&g->h_bd[i], max_streams * sizeof(BatchDev)) != cudaSuccess) return fail(REPT_E_NOMEM);
@@ -629,6 +635,8 @@ void rept_group_destroy(rept_group* g) {
     cudaFree(g->d_sd);
     cudaFree(g->d_bd);
     cudaFree(g->d_req);
+    cudaFree(g->d_pref);
+    cudaFree(g->d_cursor);
     delete g;
 }
 
@@ -725,10 +733,10 @@ int rept_group_ingest(rept_group* g, rept_state* const* hs, const uint32_t* cons
             cudaGraphDestroy(graph);
             if (e_inst != cudaSuccess) return REPT_E_CUDA;
             for (int j = 0; j < 6; ++j) g->shape[slot][j] = key[j];
-            g_launches.fetch_sub(9, std::memory_order_relaxed);  // captured, not launched
+            g_launches.fetch_sub(10, std::memory_order_relaxed);  // captured, not launched
         }
         REPT_CUDA(cudaGraphLaunch(g->exec[slot], st));
-        g_launches.fetch_add(9, std::memory_order_relaxed);
+        g_launches.fetch_add(10, std::memory_order_relaxed);
     } else {
         if ((rc = upload())) return rc;
         if ((rc = enqueue_group(g, sh, st, 0))) return rc;

@@ -591,6 +591,233 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
         if (s_proc[i]) atomicAdd(&d.proc[i], s_proc[i]);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Intersection for a group of streams with one grid: every warp may work on any stream.  The
+// per-class work lists of the k streams are concatenated (k_group_prefix writes, per class, the
+// prefix of the streams' item counts); warps claim ranges of the concatenation with one cursor per
+// class and find each item's stream from the prefix.  Closed wedges carry their stream in the
+// match queue and tau^(i) goes straight to global memory.
+
+// Per class c: pref[c * (k + 1) + i] = sum of the item counts of streams < i; cursors reset.
+__global__ void __launch_bounds__(1024) k_group_prefix(const StreamDev* __restrict__ ds, uint32_t k,
+                                                       unsigned long long* __restrict__ pref,
+                                                       unsigned long long* __restrict__ cursor) {
+    __shared__ unsigned long long warp_sum[32];
+    __shared__ unsigned long long carry;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
+    for (int c = 0; c < kBins; ++c) {
+        if (tid == 0) carry = 0ull;
+        __syncthreads();
+        for (uint32_t base = 0; base < k; base += 1024u) {
+            const uint32_t i = base + tid;
+            const unsigned long long v = i < k && ds[i].ctrl->status == 0u ? ds[i].ctrl->bin_count[c] : 0ull;
+            unsigned long long incl = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= (uint32_t)o) incl += y;
+            }
+            if (lane == 31) warp_sum[wid] = incl;
+            __syncthreads();
+            if (wid == 0) {
+                const unsigned long long w = warp_sum[lane];
+                unsigned long long wi = w;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+                    if (lane >= (uint32_t)o) wi += y;
+                }
+                warp_sum[lane] = wi - w;
+            }
+            __syncthreads();
+            const unsigned long long excl = carry + warp_sum[wid] + incl - v;
+            if (i < k) pref[c * (k + 1) + i] = excl;
+            __syncthreads();
+            if (tid == 1023) carry = excl + v;
+            __syncthreads();
+        }
+        if (tid == 0) {
+            pref[c * (k + 1) + k] = carry;
+            cursor[c] = 0ull;
+        }
+        __syncthreads();
+    }
+}
+
+struct GroupQueue {
+    uint32_t* sid;
+    uint32_t* s;
+    uint32_t* l;
+    uint32_t* w;
+    uint32_t n;
+};
+
+__device__ __forceinline__ void gq_flush(const StreamDev* __restrict__ ds, GroupQueue& q, uint32_t take) {
+    const unsigned lane = threadIdx.x & 31u;
+    if (lane < take) {
+        const uint32_t i = q.n - take + lane;
+        const StreamDev& d = ds[q.sid[i]];
+        const uint32_t s = q.s[i], l = q.l[i], w = q.w[i];
+        uint32_t found = 0;
+        for (uint32_t k = 0; k < d.groups; ++k) {
+            const uint64_t sk = group_seed(d.seed, k);
+            const uint32_t js = colour_of(s, w, sk, d.fm);
+            if (k * d.m + js < d.c && colour_of(l, w, sk, d.fm) == js) {
+                ++found;
+                atomicAdd(&d.proc[k * d.m + js], 1ull);
+            }
+        }
+        if (found) {
+            atomicAdd(&d.local[w], (unsigned long long)found);
+            atomicAdd(&d.local[s], (unsigned long long)found);
+            atomicAdd(&d.local[l], (unsigned long long)found);
+        }
+    }
+    q.n -= take;
+    __syncwarp();
+}
+
+__device__ __forceinline__ void gq_push(const StreamDev* __restrict__ ds, GroupQueue& q, bool has, uint32_t sid,
+                                        uint32_t s, uint32_t l, uint32_t w) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, has);
+    if (has) {
+        const uint32_t i = q.n + __popc(mask & ((1u << lane) - 1u));
+        q.sid[i] = sid;
+        q.s[i] = s;
+        q.l[i] = l;
+        q.w[i] = w;
+    }
+    q.n += __popc(mask);
+    __syncwarp();
+    if (q.n >= 32u) gq_flush(ds, q, 32u);
+}
+
+// Stream of item `i` of class c: the last stream whose prefix is <= i, searched from `from`.
+__device__ __forceinline__ uint32_t group_stream_of(const unsigned long long* __restrict__ pc, uint32_t k,
+                                                    unsigned long long i, uint32_t from) {
+    uint32_t sidx = from;
+    while (sidx + 1 < k && pc[sidx + 1] <= i) ++sidx;
+    return sidx;
+}
+
+__device__ __forceinline__ uint32_t group_stream_search(const unsigned long long* __restrict__ pc, uint32_t k,
+                                                        unsigned long long i) {
+    uint32_t lo = 0, hi = k - 1;  // pc[0] = 0 <= i
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (pc[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ WorkItem group_item(const StreamDev& d, int cls, unsigned long long local) {
+    return d.srec[d.ctrl->bin_start[cls] + local];
+}
+
+template <int TILE>
+__device__ __forceinline__ void group_drain_tiles(const StreamDev* __restrict__ ds, uint32_t k, int cls,
+                                                  const unsigned long long* __restrict__ pref,
+                                                  unsigned long long* __restrict__ cursor, GroupQueue& q) {
+    constexpr uint32_t kPerWarp = 32 / TILE, kRounds = 4, kGrab = kPerWarp * kRounds;
+    const unsigned lane = threadIdx.x & 31u, j = lane & (TILE - 1);
+    const unsigned long long* pc = pref + cls * (k + 1);
+    const unsigned long long total = pc[k];
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&cursor[cls], (unsigned long long)kGrab);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= total) break;
+        const uint32_t s0 = group_stream_search(pc, k, base);
+#pragma unroll 1
+        for (uint32_t r = 0; r < kRounds; ++r) {
+            const unsigned long long i = base + r * kPerWarp + lane / TILE;
+            const bool valid = i < total;
+            bool has = false;
+            uint32_t sid = 0, w = 0;
+            WorkItem x{};
+            if (valid) {
+                sid = group_stream_of(pc, k, i, s0);
+                const StreamDev& d = ds[sid];
+                x = group_item(d, cls, i - pc[sid]);
+                if (j < x.cnt_s) {
+                    const uint2 es = d.pool[4ull * x.off_s + (1ull << (x.lgs & 0xFFu)) + j];
+                    if (es.y < x.t) {
+                        uint32_t nslots = 0;
+                        has = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, es.x, nslots) < x.t;
+                        w = es.x;
+                    }
+                }
+            }
+            gq_push(ds, q, has, sid, x.s, x.l, w);
+        }
+    }
+}
+
+__device__ __forceinline__ void group_drain_warps(const StreamDev* __restrict__ ds, uint32_t k, int cls,
+                                                  const unsigned long long* __restrict__ pref,
+                                                  unsigned long long* __restrict__ cursor, uint32_t* queue,
+                                                  GroupQueue& q) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned long long* pc = pref + cls * (k + 1);
+    const unsigned long long total = pc[k];
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(&cursor[cls], 1ull);
+        i = __shfl_sync(0xFFFFFFFFu, i, 0);
+        if (i >= total) break;
+        const uint32_t sid = group_stream_search(pc, k, i);
+        const StreamDev& d = ds[sid];
+        const WorkItem x = group_item(d, cls, i - pc[sid]);
+        const uint32_t lg_l = x.lgs >> 8, n_s = x.cnt_s;
+        const unsigned long long base_l = 4ull * x.off_l;
+        const uint4* list = reinterpret_cast<const uint4*>(d.pool + 4ull * x.off_s + (1ull << (x.lgs & 0xFFu)));
+        for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
+            uint32_t n_q = 0;
+            const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+            for (uint32_t half = 0; half < 2; ++half) {
+                const uint32_t jj = j0 + 64u * half + 2u * lane;
+                uint4 e4 = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
+                if (jj < n_s) e4 = list[jj >> 1];
+                const bool a1 = jj < n_s && e4.y < x.t, a2 = jj + 1u < n_s && e4.w < x.t;
+                const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
+                if (a1) queue[n_q + __popc(m1 & below)] = e4.x;
+                n_q += __popc(m1);
+                if (a2) queue[n_q + __popc(m2 & below)] = e4.z;
+                n_q += __popc(m2);
+            }
+            __syncwarp();
+            for (uint32_t k0 = 0; k0 < n_q; k0 += 32u) {
+                bool has = false;
+                uint32_t w = 0;
+                if (k0 + lane < n_q) {
+                    w = queue[k0 + lane];
+                    uint32_t nslots = 0;
+                    has = table_find(d.pool, base_l, lg_l, w, nslots) < x.t;
+                }
+                gq_push(ds, q, has, sid, x.s, x.l, w);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 5) k_intersect_group(const StreamDev* __restrict__ ds, uint32_t k,
+                                                            const unsigned long long* __restrict__ pref,
+                                                            unsigned long long* __restrict__ cursor) {
+    __shared__ uint32_t s_queue[256 / 32][kQueue];
+    __shared__ uint32_t s_match[256 / 32][4][kMatchQ];
+    const unsigned wid = threadIdx.x >> 5;
+    uint32_t* queue = s_queue[wid];
+    GroupQueue q{s_match[wid][0], s_match[wid][1], s_match[wid][2], s_match[wid][3], 0u};
+    group_drain_warps(ds, k, 5, pref, cursor, queue, q);
+    group_drain_warps(ds, k, 4, pref, cursor, queue, q);
+    group_drain_tiles<32>(ds, k, 3, pref, cursor, q);
+    group_drain_tiles<16>(ds, k, 2, pref, cursor, q);
+    group_drain_tiles<8>(ds, k, 1, pref, cursor, q);
+    group_drain_tiles<4>(ds, k, 0, pref, cursor, q);
+    if (q.n) gq_flush(ds, q, q.n);
+}
+
 // Kernel entry points.  Each batch kernel exists twice: for one stream (state and batch passed by
 // value) and for many streams at once (`_multi`: blockIdx.y selects the stream, whose state and batch
 // descriptors are read from device arrays; blockIdx.x / gridDim.x then range over that stream's blocks).
