@@ -11,6 +11,12 @@ the timed region starts; the edge list (126 MB) plus the device state
 (~0.9 GB) exceed the 129 MB L2, so no explicit flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--c 100]
+                  [--workload rmat_s20|powerlaw_20k|powerlaw_4m|batched|serve]
+
+The other workloads: powerlaw_20k (Chung-Lu, 20,000 nodes, m = c = 10) and powerlaw_4m (Chung-Lu,
+2^22 nodes, 64 * 2^20 edges, m = 20, c = 100 in five hash groups) in the same single-stream form;
+batched (256 independent streams, the batched path against a loop of the plain path); serve (a
+Poisson request trace with continuous batching, p50/p99 latency).
 
 Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank counts its
 own replica of the stream with its own hash seed (the plain path has no
@@ -45,6 +51,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--c", type=int, default=100, help="processors (the workload runs at c=30 and c=100)")
+    ap.add_argument("--workload", default="rmat_s20",
+                    choices=["rmat_s20", "powerlaw_20k", "powerlaw_4m", "batched", "serve"],
+                    help="rmat_s20 (default, the headline), powerlaw_20k, powerlaw_4m, batched (256 streams, "
+                         "batched vs a loop of the plain path), serve (Poisson request trace)")
+    ap.add_argument("--streams", type=int, default=256, help="batched: number of streams")
+    ap.add_argument("--requests", type=int, default=1000, help="serve: number of requests")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -157,19 +169,27 @@ def hbm_peak():
 
 
 # --------------------------------------------------------------------------- workload
-def workload():
+WORKLOADS = {
+    # name: (m, c, description)
+    "rmat_s20": (100, None, "R-MAT scale 20, ef 16"),
+    "powerlaw_20k": (10, 10, "Chung-Lu 20,000 nodes, exponent 2.3, 200,000 edges"),
+    "powerlaw_4m": (20, 100, "Chung-Lu 2^22 nodes, exponent 2.1, degree cap 50,000, 64 * 2^20 edges"),
+}
+
+
+def workload(name="rmat_s20"):
     from paper_1811_09136_gb300 import graphgen
-    return graphgen.cached("rmat_s20")
+    return graphgen.cached(name)
 
 
-def cpu_sample_rate(s, c, budget_s=15.0):
+def cpu_sample_rate(s, m, c, budget_s=15.0):
     """The oracle (sequential CPU REPT) on a prefix of the same stream, sized to ~budget_s seconds."""
     import oracle
     n_edges = 1 << 14
     spent = 0.0
     while True:
         t = time.perf_counter()
-        oracle.rept_stream(s.src[:n_edges], s.dst[:n_edges], s.n_nodes, M, c, SEED, pair_counters=False)
+        oracle.rept_stream(s.src[:n_edges], s.dst[:n_edges], s.n_nodes, m, c, SEED, pair_counters=False)
         spent = time.perf_counter() - t
         if spent > budget_s / 4 or n_edges >= len(s):
             break
@@ -182,23 +202,26 @@ def run_reference(args, world, rank, pg):
     """The CPU oracle, as it stands, on the host cores: a bounded prefix of the stream per step."""
     if rank != 0:
         return 0
-    s = workload()
+    name = args.workload if args.workload in WORKLOADS else "rmat_s20"
+    s = workload(name)
+    m, c, desc = WORKLOADS[name]
+    c = args.c if c is None else c
     import oracle
-    n_edges, t1 = cpu_sample_rate(s, args.c, budget_s=8.0)
+    n_edges, _ = cpu_sample_rate(s, m, c, budget_s=8.0)
     for _ in range(args.warmup):
-        oracle.rept_stream(s.src[:n_edges], s.dst[:n_edges], s.n_nodes, M, args.c, SEED, pair_counters=False)
+        oracle.rept_stream(s.src[:n_edges], s.dst[:n_edges], s.n_nodes, m, c, SEED, pair_counters=False)
     t = time.perf_counter()
     for _ in range(args.steps):
-        oracle.rept_stream(s.src[:n_edges], s.dst[:n_edges], s.n_nodes, M, args.c, SEED, pair_counters=False)
+        oracle.rept_stream(s.src[:n_edges], s.dst[:n_edges], s.n_nodes, m, c, SEED, pair_counters=False)
     el = time.perf_counter() - t
     v = args.steps * n_edges / el
-    sample = f"first {n_edges} edges of the stream per step (sequential REPT, {args.c} processors)"
+    sample = f"first {n_edges} edges of the stream per step (sequential REPT, {c} processors)"
     line = {"metric": METRIC, "value": v, "unit": "edges/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"rmat_s20 (scale 20, ef 16, {len(s)} edges), m={M}, c={args.c}, seed={SEED}",
-                       "sample": sample},
+            "config": {"workload": f"{name}: {desc}, {len(s)} edges, m={m}, c={c}, seed={SEED}, "
+                                   f"batches of {BATCH}", "sample": sample},
             "cpu_baseline": {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -206,19 +229,17 @@ def run_reference(args, world, rank, pg):
 
 
 # --------------------------------------------------------------------------- our arm
-def run_ours(args, world, rank, local, pg):
-    import torch
-    from paper_1811_09136_gb300 import rept
+def single_stream_setup(args, rank):
+    name = args.workload
+    s = workload(name)
+    m, c, desc = WORKLOADS[name]
+    c = args.c if c is None else c
+    return s, m, c, SEED + rank, desc  # independent replica (own hash seed) per rank
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    s = workload()
-    T = len(s)
-    seed = SEED + rank  # independent replica per rank
-    stream = torch.cuda.current_stream(dev)
-    src = torch.from_numpy(s.src.view(np.int32)).to(dev)
-    dst = torch.from_numpy(s.dst.view(np.int32)).to(dev)
-    r = rept.ReptStream(s.n_nodes, M, args.c, seed, expected_edges=T, max_batch=BATCH, flags=rept.FLAG_PROFILE)
+
+def time_single_stream(r, src, dst, T, steps, stream):
+    """`steps` full passes (reset, all batches, estimates) bracketed by CUDA events on `stream`."""
+    import torch
 
     def step():
         r.reset()
@@ -226,6 +247,30 @@ def run_ours(args, world, rank, local, pg):
             r.ingest(src[off:off + BATCH], dst[off:off + BATCH])
         return r.estimates(local=True)
 
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    g = None
+    for _ in range(steps):
+        g, _ = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), g, step
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+    from paper_1811_09136_gb300 import rept
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s, m, c, seed, desc = single_stream_setup(args, rank)
+    T = len(s)
+    stream = torch.cuda.current_stream(dev)
+    src = torch.from_numpy(s.src.view(np.int32)).to(dev)
+    dst = torch.from_numpy(s.dst.view(np.int32)).to(dev)
+    r = rept.ReptStream(s.n_nodes, m, c, seed, expected_edges=T, max_batch=BATCH, flags=rept.FLAG_PROFILE)
+
+    _, _, step = time_single_stream(r, src, dst, T, 0, stream)
     for _ in range(args.warmup):
         step()
     r.kernel_times(clear=True)
@@ -234,14 +279,8 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize(dev)
     clocks.start()
     launches0 = rept.kernel_launches()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        g, _ = step()
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
+    ms, g, _ = time_single_stream(r, src, dst, T, args.steps, stream)
     barrier(pg)
-    ms = ev0.elapsed_time(ev1)
     launches = rept.kernel_launches() - launches0
     clk = clocks.stop()
     kt = r.kernel_times(clear=True)
@@ -249,7 +288,7 @@ def run_ours(args, world, rank, local, pg):
     proc, _ = r.counts()
 
     # ---- algorithmic bytes of the intersection kernel (one extra, untimed pass with work counters)
-    with rept.ReptStream(s.n_nodes, M, args.c, seed, expected_edges=T, max_batch=BATCH,
+    with rept.ReptStream(s.n_nodes, m, c, seed, expected_edges=T, max_batch=BATCH,
                          flags=rept.FLAG_WORK_COUNTERS) as rw:
         for off in range(0, T, BATCH):
             rw.ingest(src[off:off + BATCH], dst[off:off + BATCH])
@@ -261,6 +300,15 @@ def run_ours(args, world, rank, local, pg):
     k3_ms_step = k3_ms / args.steps
     peak, peak_src = hbm_peak()
     achieved = k3_bytes / (k3_ms_step * 1e-3) / 1e9
+
+    # ---- the same stream at c = 30 (the workload is quoted at c = 30 and c = 100)
+    other_c = None
+    if args.workload == "rmat_s20" and c != 30:
+        with rept.ReptStream(s.n_nodes, m, 30, seed, expected_edges=T, max_batch=BATCH) as r30:
+            _, _, step30 = time_single_stream(r30, src, dst, T, 0, stream)
+            step30()
+            ms30, g30, _ = time_single_stream(r30, src, dst, T, 3, stream)
+        other_c = {"c": 30, "edges_per_s": 3 * T / (ms30 * 1e-3), "ms_per_step": ms30 / 3, "tau_hat": g30}
 
     # ---- end to end through the C-ABI from pinned host buffers
     e2e = None
@@ -287,9 +335,9 @@ def run_ours(args, world, rank, local, pg):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_edges, el = cpu_sample_rate(s, args.c)
+        n_edges, el = cpu_sample_rate(s, m, c)
         cpu = {"value": n_edges / el, "unit": "edges/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {n_edges} edges of the same stream (sequential REPT, {args.c} processors); "
+               "sample": f"first {n_edges} edges of the same stream (sequential REPT, {c} processors); "
                          f"early edges meet smaller sets, so this overstates the oracle's full-stream rate"}
 
     if rank == 0:
@@ -298,11 +346,12 @@ def run_ours(args, world, rank, local, pg):
             "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
-            "config": {"workload": f"rmat_s20: R-MAT scale 20, ef 16, {T} edges, m={M}, c={args.c}, "
-                                   f"seed={SEED}, batches of {BATCH}",
+            "config": {"workload": f"{args.workload}: {desc}, {T} edges, m={m}, c={c}, seed={SEED}, "
+                                   f"batches of {BATCH}",
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs and state larger than L2 (no flush)",
-                       "tau_hat": g, "semi_triangles": int(proc.sum())},
+                       "l2": "inputs and state larger than L2 (no flush)" if T * 8 > (129 << 20) else
+                             "working set fits in L2 (no flush)",
+                       "tau_hat": g, "semi_triangles": int(proc.sum()), "other_c": other_c},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_intersect",
                          "peak_source": peak_src, "algorithmic_bytes_per_step": k3_bytes,
@@ -317,6 +366,67 @@ def run_ours(args, world, rank, local, pg):
     return 0
 
 
+def run_batched_mix(args, world, rank, local, pg):
+    """256 independent streams: the batched path (one launch per step for all streams, CUDA graphs)
+    against a loop of the plain single-stream path, at identical counts.  Batch size and tile width
+    are autotuned on a 16-stream sample of the mix."""
+    import torch
+    from paper_1811_09136_gb300 import batched
+
+    torch.cuda.set_device(local)
+    specs = batched.mix_specs(args.streams, seed=1000 + 7919 * rank)
+    t = time.perf_counter()
+    streams = batched.generate_all(specs)
+    gen_s = time.perf_counter() - t
+    params = [(sp.m, sp.m, sp.hash_seed) for sp in specs]
+    E = sum(len(x) for x in streams)
+    sample = sorted(range(len(streams)), key=lambda i: len(streams[i]))[::max(1, len(streams) // 16)][:16]
+    b, tm, timings = batched.autotune([streams[i] for i in sample], [params[i] for i in sample],
+                                      key=f"mix{args.streams}")
+    res_b, t_b = batched.run_batched(streams, params, batch=b, tile_max=tm)
+    res_p, t_p = batched.run_plain(streams, params, batch=b, tile_max=tm)
+    same = all(np.array_equal(x.proc, y.proc) and np.array_equal(x.local, y.local) for x, y in zip(res_b, res_p))
+    assert same, "batched and plain counts differ"
+    t_b = max_over_ranks(pg, t_b)
+    t_p = max_over_ranks(pg, t_p)
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * E / t_b, "unit": "edges/s", "n_gpus": world, "steps": 1,
+                "warmup": 0, "ms_per_step": 1e3 * t_b, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
+                "config": {"workload": f"batched: {args.streams} streams (R-MAT / Chung-Lu, n log-uniform in "
+                                       f"[1e4, 2e6], 10-40 edges per node, p in {{0.1, 0.05, 0.01}}, c = m), "
+                                       f"{E} edges", "batch": b, "tile_max": tm, "autotune_s": timings,
+                           "generation_s": gen_s},
+                "plain_loop": {"value": world * E / t_p, "unit": "edges/s", "ms": 1e3 * t_p},
+                "batched_over_plain": t_p / t_b, "identical_counts": same}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving(args, world, rank, local, pg):
+    """A Poisson request trace served with continuous batching: aggregate edges/s and latency."""
+    import torch
+    from paper_1811_09136_gb300 import serve
+
+    torch.cuda.set_device(local)
+    t = time.perf_counter()
+    reqs = serve.build_trace(n_requests=args.requests, seed=5 + rank)
+    gen_s = time.perf_counter() - t
+    rep = serve.serve(reqs)
+    sm = rep.summary()
+    if rank == 0:
+        line = {"metric": METRIC, "value": sm["edges_per_s"] * world, "unit": "edges/s", "n_gpus": world,
+                "steps": 1, "warmup": 0, "ms_per_step": 1e3 * sm["makespan_s"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
+                "config": {"workload": f"serve: {args.requests} requests, Poisson arrivals at 200/s, streams "
+                                       f"from the batched mix plus an R-MAT scale-24 ef-16 stream (p=0.01, "
+                                       f"c=100) every 50th request, chunks of 2^16-2^20",
+                           "generation_s": gen_s},
+                "serving": sm}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     world, rank, local, pg = dist_setup(args)
@@ -324,6 +434,10 @@ def main():
         print(f"warning: --gpus {args.gpus} but WORLD_SIZE {world}", file=sys.stderr)
     if args.impl == "reference":
         rc = run_reference(args, world, rank, pg)
+    elif args.workload == "batched":
+        rc = run_batched_mix(args, world, rank, local, pg)
+    elif args.workload == "serve":
+        rc = run_serving(args, world, rank, local, pg)
     else:
         rc = run_ours(args, world, rank, local, pg)
     if pg is not None:
