@@ -358,7 +358,8 @@ def run_ours(args, world, rank, local, pg):
                          "kernel_ms_per_step": k3_ms_step, "launches_per_step": k3_n // args.steps},
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
             "work": {k: st[k] for k in ("small_entries", "small_slots", "probes", "probe_slots", "wedges",
-                                        "counted", "stored_edges")},
+                                        "counted", "stored_edges", "class_items", "class_probes",
+                                        "class_cycles")},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -101,6 +101,10 @@ typedef struct rept_stats {
     uint64_t probe_slots;    /* slots read by those probes */
     uint64_t wedges;         /* closed wedges found in the union adjacency (both edges older than the edge) */
     uint64_t counted;        /* (wedge, hash group) pairs counted for some processor */
+    uint64_t class_items[6]; /* edges per intersection work class (smaller endpoint with <= 4, 8, 16,
+                                32, 256, more entries) */
+    uint64_t class_probes[6];  /* probes issued per work class */
+    uint64_t class_cycles[6];  /* warp-cycles spent per work class (clock64, summed over warps) */
 } rept_stats;
 
 typedef struct rept_state rept_state;

@@ -448,6 +448,11 @@ int rept_get_stats(rept_state* s, rept_stats* out, void* stream) {
     out->probe_slots = s->h_ctrl->probe_slots;
     out->wedges = s->h_ctrl->wedges;
     out->counted = s->h_ctrl->counted;
+    for (int c = 0; c < kBins; ++c) {
+        out->class_items[c] = s->h_ctrl->class_items[c];
+        out->class_probes[c] = s->h_ctrl->class_probes[c];
+        out->class_cycles[c] = s->h_ctrl->class_cycles[c];
+    }
     return rc;
 }
 

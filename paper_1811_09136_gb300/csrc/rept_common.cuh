@@ -94,6 +94,7 @@ struct Ctrl {
     unsigned int pad;
     // work counters of k_intersect<true> (see rept_stats)
     unsigned long long small_entries, small_slots, probes, probe_slots, wedges, counted;
+    unsigned long long class_items[6], class_probes[6], class_cycles[6];
     // per-batch work list of k_intersect: class c occupies items[bin_start[c] .. + bin_count[c])
     unsigned long long bin_start[kBins];
     unsigned long long bin_count[kBins];

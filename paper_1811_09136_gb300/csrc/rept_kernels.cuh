@@ -560,13 +560,38 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
     MatchQueue mq{s_match[wid][0], s_match[wid][1], s_match[wid][2], 0u};
     Work wk;
     if (d.ctrl->status == 0u) {
+        // WORK: per class, the probes issued and the warp-cycles spent (clock64 around each drain)
+        long long t0 = WORK ? clock64() : 0;
+        unsigned long long p0 = wk.probes;
+        auto mark = [&](int cls) {
+            if (WORK) {
+                const long long t1 = clock64();
+                const unsigned long long p1 = wk.probes;
+                unsigned long long pr = p1 - p0;
+                for (int o = 16; o > 0; o >>= 1) pr += __shfl_down_sync(0xFFFFFFFFu, pr, o);
+                if (lane == 0) {
+                    atomicAdd(&d.ctrl->class_cycles[cls], (unsigned long long)(t1 - t0));
+                    atomicAdd(&d.ctrl->class_probes[cls], pr);
+                }
+                t0 = t1;
+                p0 = p1;
+            }
+        };
         drain_warp_bin<WORK>(d, 5, s_proc, queue, mq, wk);
+        mark(5);
         drain_warp_bin<WORK>(d, 4, s_proc, queue, mq, wk);
+        mark(4);
         drain_tile_bin<32, WORK>(d, 3, s_proc, mq, wk);
+        mark(3);
         drain_tile_bin<16, WORK>(d, 2, s_proc, mq, wk);
+        mark(2);
         drain_tile_bin<8, WORK>(d, 1, s_proc, mq, wk);
+        mark(1);
         drain_tile_bin<4, WORK>(d, 0, s_proc, mq, wk);
+        mark(0);
         if (mq.n) mq_flush<WORK>(d, mq, mq.n, s_proc, wk);
+        if (WORK && blockIdx.x == 0 && threadIdx.x < kBins)
+            d.ctrl->class_items[threadIdx.x] += d.ctrl->bin_count[threadIdx.x];
     }
     if (WORK) {
         for (int o = 16; o > 0; o >>= 1) {

@@ -41,7 +41,9 @@ class Stats(ctypes.Structure):
     _fields_ = [("edges", ctypes.c_uint64), ("self_loops", ctypes.c_uint64), ("stored_edges", ctypes.c_uint64),
                 ("pool_slots", ctypes.c_uint64), ("pool_used", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("small_entries", ctypes.c_uint64), ("small_slots", ctypes.c_uint64), ("probes", ctypes.c_uint64),
-                ("probe_slots", ctypes.c_uint64), ("wedges", ctypes.c_uint64), ("counted", ctypes.c_uint64)]
+                ("probe_slots", ctypes.c_uint64), ("wedges", ctypes.c_uint64), ("counted", ctypes.c_uint64),
+                ("class_items", ctypes.c_uint64 * 6), ("class_probes", ctypes.c_uint64 * 6),
+                ("class_cycles", ctypes.c_uint64 * 6)]
 
 
 _lock = threading.Lock()
@@ -219,7 +221,11 @@ class ReptStream:
     def stats(self, stream=None) -> dict:
         st = Stats()
         _check(self._lib.rept_get_stats(self._h, ctypes.byref(st), _cur_stream(stream)), "rept_get_stats")
-        return {k: int(getattr(st, k)) for k, _ in Stats._fields_}
+        out = {}
+        for k, _ in Stats._fields_:
+            v = getattr(st, k)
+            out[k] = [int(x) for x in v] if hasattr(v, "__len__") else int(v)
+        return out
 
     def kernel_times(self, clear: bool = False) -> dict:
         """{kernel: (milliseconds, launches)} from CUDA events (needs FLAG_PROFILE)."""
