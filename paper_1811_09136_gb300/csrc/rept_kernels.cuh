@@ -448,6 +448,10 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
 // smaller table (two 16-byte loads per lane), packs the entries older than the edge into the warp's
 // shared-memory key queue, and then probes them with all 32 lanes.
 constexpr int kQueue = 128;
+#ifndef REPT_PROBES_PER_LANE
+#define REPT_PROBES_PER_LANE 2
+#endif
+constexpr int kProbesPerLane = REPT_PROBES_PER_LANE;  // probes each lane keeps in flight (warp path)
 
 template <bool WORK>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, unsigned long long* s_proc,
@@ -474,32 +478,40 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
             n_q += __popc(m2);
         }
         __syncwarp();
-        // two queued neighbours per lane: both home buckets are loaded before either is examined
+        // kProbesPerLane queued neighbours per lane: all their home buckets are loaded before any is
+        // examined, then the stream indices of the hits
         const uint32_t* keys_l = reinterpret_cast<const uint32_t*>(d.pool + base_l);
         const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
         const uint32_t cap_l = 1u << lg_l;
-        for (uint32_t k0 = 0; k0 < n_q; k0 += 64u) {
-            const bool v1 = k0 + lane < n_q, v2 = k0 + 32u + lane < n_q;
-            const uint32_t w1 = v1 ? queue[k0 + lane] : kEmptyId, w2 = v2 ? queue[k0 + 32u + lane] : kEmptyId;
-            const uint32_t h1 = home_slot(w1, lg_l), h2 = home_slot(w2, lg_l);
-            uint4 b1 = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId), b2 = b1;
-            if (v1) b1 = buckets_l[h1 >> 2];
-            if (v2) b2 = buckets_l[h2 >> 2];
-            const int at1 = b1.x == w1 ? 0 : b1.y == w1 ? 1 : b1.z == w1 ? 2 : b1.w == w1 ? 3 : -1;
-            const int at2 = b2.x == w2 ? 0 : b2.y == w2 ? 1 : b2.z == w2 ? 2 : b2.w == w2 ? 3 : -1;
-            const bool full1 = b1.x != kEmptyId && b1.y != kEmptyId && b1.z != kEmptyId && b1.w != kEmptyId;
-            const bool full2 = b2.x != kEmptyId && b2.y != kEmptyId && b2.z != kEmptyId && b2.w != kEmptyId;
-            uint32_t r1 = kEmptyId, r2 = kEmptyId, n1 = 4u, n2 = 4u;
-            if (v1 && at1 >= 0) r1 = keys_l[cap_l + h1 + (uint32_t)at1];
-            if (v2 && at2 >= 0) r2 = keys_l[cap_l + h2 + (uint32_t)at2];
-            if (v1 && at1 < 0 && full1) r1 = table_find(d.pool, base_l, lg_l, w1, n1);  // rare: read on
-            if (v2 && at2 < 0 && full2) r2 = table_find(d.pool, base_l, lg_l, w2, n2);
-            if (WORK) {
-                if (v1) { ++wk.probes; wk.pslots += n1; }
-                if (v2) { ++wk.probes; wk.pslots += n2; }
+        for (uint32_t k0 = 0; k0 < n_q; k0 += 32u * kProbesPerLane) {
+            uint32_t w[kProbesPerLane], h[kProbesPerLane], r[kProbesPerLane];
+            uint4 bk[kProbesPerLane];
+#pragma unroll
+            for (int p = 0; p < kProbesPerLane; ++p) {
+                const bool v = k0 + 32u * p + lane < n_q;
+                w[p] = v ? queue[k0 + 32u * p + lane] : kEmptyId;
+                h[p] = home_slot(w[p], lg_l);
+                bk[p] = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
+                if (v) bk[p] = __ldg(&buckets_l[h[p] >> 2]);
             }
-            mq_push<WORK>(d, mq, v1 && r1 < x.t, x.s, x.l, w1, s_proc, wk);
-            mq_push<WORK>(d, mq, v2 && r2 < x.t, x.s, x.l, w2, s_proc, wk);
+#pragma unroll
+            for (int p = 0; p < kProbesPerLane; ++p) {
+                const uint4 b = bk[p];
+                const int at = b.x == w[p] ? 0 : b.y == w[p] ? 1 : b.z == w[p] ? 2 : b.w == w[p] ? 3 : -1;
+                r[p] = kEmptyId;
+                if (w[p] != kEmptyId) {
+                    uint32_t ns = 4u;
+                    if (at >= 0) {
+                        r[p] = __ldg(&keys_l[cap_l + h[p] + (uint32_t)at]);
+                    } else if (b.x != kEmptyId && b.y != kEmptyId && b.z != kEmptyId && b.w != kEmptyId) {
+                        r[p] = table_find(d.pool, base_l, lg_l, w[p], ns);  // rare: the bucket is full
+                    }
+                    if (WORK) { ++wk.probes; wk.pslots += ns; }
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < kProbesPerLane; ++p)
+                mq_push<WORK>(d, mq, w[p] != kEmptyId && r[p] < x.t, x.s, x.l, w[p], s_proc, wk);
         }
         __syncwarp();
     }
