@@ -308,10 +308,12 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
         probe.c = cfg->c;
         probe.stage_keys = stage_keys_setting();
         const size_t hs = hub_smem_bytes(probe);
+        // the limit is a property of the kernel, shared by every handle: allow the largest any handle uses
+        const int hub_max = (int)(((kMaxProcessors * 8u + 15u) & ~15u) + 32768u * 4u);
         int hub_per_sm = 0;
-        if (cudaFuncSetAttribute(k_intersect_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs) !=
+        if (cudaFuncSetAttribute(k_intersect_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hub_max) !=
                 cudaSuccess ||
-            cudaFuncSetAttribute(k_intersect_hub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hs) !=
+            cudaFuncSetAttribute(k_intersect_hub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hub_max) !=
                 cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&hub_per_sm, k_intersect_hub<false>, 256, hs) != cudaSuccess)
             return fail(REPT_E_CUDA);

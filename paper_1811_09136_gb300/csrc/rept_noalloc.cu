@@ -145,7 +145,7 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
         const int grid_i = (int)(want_i < (unsigned long long)sms * 4 ? want_i : (unsigned long long)sms * 4);
         const size_t hub_smem = ((c * 8u + 15u) & ~15u) + (size_t)kStageKeys * 4u;
         NA_CUDA(cudaFuncSetAttribute(k_intersect_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)hub_smem));
+                                     (int)(((kMaxProcessors * 8u + 15u) & ~15u) + 32768u * 4u)));
         k_intersect_hub<false><<<sms * 2, 256, hub_smem, st>>>(d, b);
         k_intersect<false><<<grid_i, 256, c * sizeof(unsigned long long), st>>>(d, b);
         NA_CUDA(cudaPeekAtLastError());
