@@ -36,6 +36,8 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
            *sorted(glob.glob(os.path.join(CSRC, "*.cu")))]
     if verbose_ptxas:
         cmd[1:1] = ["-Xptxas", "-v"]
+    if os.environ.get("REPT_DEBUG_BOUNDS"):
+        cmd[1:1] = ["-DREPT_DEBUG_BOUNDS"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH

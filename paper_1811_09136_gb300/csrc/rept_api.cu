@@ -43,6 +43,9 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
     } while (0)
 
 int status_to_code(unsigned st) {
+#ifdef REPT_DEBUG_BOUNDS
+    (void)0;
+#endif
     if (st & kStRange) return REPT_E_RANGE;
     if (st & kStCapacity) return REPT_E_CAPACITY;
     if (st & kStTimeout) return REPT_E_TIMEOUT;
@@ -262,6 +265,11 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
 int sync_status(rept_state* s, cudaStream_t st) {
     int rc = read_ctrl(s, st);
     if (rc) return rc;
+#ifdef REPT_DEBUG_BOUNDS
+    if (s->h_ctrl->dbg[3])
+        std::fprintf(stderr, "rept bounds check %llu failed: index %llu bound %llu (%llu times)\n",
+                     s->h_ctrl->dbg[0], s->h_ctrl->dbg[1], s->h_ctrl->dbg[2], s->h_ctrl->dbg[3]);
+#endif
     return status_to_code(s->h_ctrl->status);
 }
 

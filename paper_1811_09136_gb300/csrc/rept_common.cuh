@@ -112,6 +112,7 @@ struct Ctrl {
     unsigned long long bin_next[kBins];
     unsigned long long n_runs;    // runs of equal warp-class keys (k_intersect_hub), at most kRunMax items
     unsigned long long run_next;  // claim cursor over the runs
+    unsigned long long dbg[4];  // REPT_DEBUG_BOUNDS builds: first failed check {where, index, bound, count}
     unsigned long long n_big;   // nodes whose table (32..2048 slots) k_rehash_big moves, a warp each
     unsigned long long n_huge;  // nodes whose table (>= 4096 slots) k_rehash_huge moves, a block each
     unsigned long long huge_next;
@@ -160,6 +161,23 @@ struct BatchDev {
     unsigned long long n;
     unsigned long long t0;  // stream index of src[0], dst[0]
 };
+
+// Bounds checks of the REPT_DEBUG_BOUNDS build: a failed check records {where, index, bound} once and
+// counts, and the caller skips the access.  Release builds compile them away.
+#ifdef REPT_DEBUG_BOUNDS
+__device__ __forceinline__ bool dbg_ok(Ctrl* c, unsigned where, unsigned long long idx, unsigned long long bound) {
+    if (idx < bound) return true;
+    if (atomicAdd(&c->dbg[3], 1ull) == 0ull) {
+        c->dbg[0] = where;
+        c->dbg[1] = idx;
+        c->dbg[2] = bound;
+    }
+    return false;
+}
+#define REPT_CHECK(c, where, idx, bound) dbg_ok((c), (where), (idx), (bound))
+#else
+#define REPT_CHECK(c, where, idx, bound) true
+#endif
 
 // One output step of SplitMix64 from state x (Steele, Lea, Flood 2014).
 __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {

@@ -394,7 +394,7 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
             atomicAdd(&s_proc[k * d.m + js], 1ull);
         }
     }
-    if (found) {
+    if (found && REPT_CHECK(d.ctrl, 6, (unsigned long long)max(w, max(s, l)), d.n_nodes)) {
         atomicAdd(&d.local[w], (unsigned long long)found);
         atomicAdd(&d.local[s], (unsigned long long)found);
         atomicAdd(&d.local[l], (unsigned long long)found);
@@ -430,7 +430,7 @@ __device__ __forceinline__ void mq_push(const StreamDev& d, MatchQueue& q, bool 
                                         uint32_t w, unsigned long long* s_proc, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, has);
-    if (has) {
+    if (has && REPT_CHECK(d.ctrl, 7, q.n + __popc(mask & ((1u << lane) - 1u)), kMatchQ)) {
         const uint32_t i = q.n + __popc(mask & ((1u << lane) - 1u));
         q.s[i] = s;
         q.l[i] = l;
@@ -490,12 +490,14 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
         for (uint32_t half = 0; half < 2; ++half) {
             const uint32_t jj = j0 + 64u * half + 2u * lane;
             uint4 q = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-            if (jj < n_s) q = list[jj >> 1];
+            if (jj < n_s && REPT_CHECK(d.ctrl, 4, 4ull * x.off_s + (1ull << (x.lgs & 0xFFu)) + jj + 1,
+                                       4ull * d.pool_quads))
+                q = list[jj >> 1];
             const bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
             const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
-            if (a1) queue[n_q + __popc(m1 & below)] = q.x;
+            if (a1 && REPT_CHECK(d.ctrl, 8, n_q + __popc(m1 & below), kQueue)) queue[n_q + __popc(m1 & below)] = q.x;
             n_q += __popc(m1);
-            if (a2) queue[n_q + __popc(m2 & below)] = q.z;
+            if (a2 && REPT_CHECK(d.ctrl, 8, n_q + __popc(m2 & below), kQueue)) queue[n_q + __popc(m2 & below)] = q.z;
             n_q += __popc(m2);
         }
         __syncwarp();
@@ -514,7 +516,9 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
                 w[p] = v ? queue[k0 + 32u * p + lane] : kEmptyId;
                 h[p] = home_slot(w[p], lg_l);
                 bk[p] = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-                if (v) bk[p] = buckets_l[h[p] >> 2];
+                if (v && REPT_CHECK(d.ctrl, 3, h[p], staged ? d.stage_keys : cap_l) &&
+                    REPT_CHECK(d.ctrl, 4, 4ull * x.off_l + cap_l, 4ull * d.pool_quads))
+                    bk[p] = buckets_l[h[p] >> 2];
             }
 #pragma unroll
             for (int p = 0; p < kProbesPerLane; ++p) {
@@ -661,7 +665,6 @@ __device__ __forceinline__ void k_intersect_hub_body(const StreamDev& d, const B
     __shared__ uint32_t s_match[256 / 32][3][kMatchQ];
     __shared__ unsigned long long s_r;
     __shared__ uint32_t s_next;
-    (void)b;
     for (uint32_t i = threadIdx.x; i < d.c; i += blockDim.x) s_proc[i] = 0ull;
     const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     uint32_t* queue = s_queue[wid];
@@ -677,11 +680,13 @@ __device__ __forceinline__ void k_intersect_hub_body(const StreamDev& d, const B
         __syncthreads();
         const unsigned long long r = s_r;
         if (r >= n_runs) break;
+        if (!REPT_CHECK(d.ctrl, 1, n_runs - 1 - r, b.n)) break;
         const uint2 run = d.runs[n_runs - 1 - r];  // the larger class's runs sit at the end
+        if (!REPT_CHECK(d.ctrl, 2, (unsigned long long)run.x + run.y, b.n + 1)) break;
         const WorkItem x0 = d.srec[run.x];
         const uint32_t cap0 = 1u << (x0.lgs >> 8);
         const bool staged = cap0 <= d.stage_keys;
-        if (staged) {
+        if (staged && REPT_CHECK(d.ctrl, 11, 4ull * x0.off_l + cap0, 4ull * d.pool_quads + 1)) {
             const uint4* src = reinterpret_cast<const uint4*>(d.pool + 4ull * x0.off_l);
             uint4* dst = reinterpret_cast<uint4*>(stage);
             for (uint32_t q = threadIdx.x; q < cap0 / 4u; q += blockDim.x) dst[q] = src[q];
