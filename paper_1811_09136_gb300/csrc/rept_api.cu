@@ -248,10 +248,7 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
     const size_t smem = s->cfg.c * sizeof(unsigned long long);
     const size_t hub_smem = hub_smem_bytes(s->d);
     if (s->cfg.flags & REPT_FLAG_WORK_COUNTERS)
-        rc = timed_launch(s, REPT_K_INTERSECT, st, [&] {
-            k_intersect_hub<true><<<s->grid_hub, 256, hub_smem, st>>>(s->d, b);
-            k_intersect<true><<<grid_i, 256, smem, st>>>(s->d, b);
-        }, 2);
+        rc = timed_launch(s, REPT_K_INTERSECT, st, [&] { k_intersect<true><<<grid_i, 256, smem, st>>>(s->d, b); });
     else
         rc = timed_launch(s, REPT_K_INTERSECT, st, [&] {
             k_intersect_hub<false><<<s->grid_hub, 256, hub_smem, st>>>(s->d, b);
@@ -320,8 +317,6 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
         const int hub_max = (int)(((kMaxProcessors * 8u + 15u) & ~15u) + 32768u * 4u);
         int hub_per_sm = 0;
         if (cudaFuncSetAttribute(k_intersect_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hub_max) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_intersect_hub<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hub_max) !=
                 cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&hub_per_sm, k_intersect_hub<false>, 256, hs) != cudaSuccess)
             return fail(REPT_E_CUDA);

@@ -615,7 +615,14 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
                 p0 = p1;
             }
         };
-        // classes 4 and 5 (a warp per edge) are served by k_intersect_hub
+        // classes 4 and 5 (a warp per edge) are served by k_intersect_hub; the work-counting pass
+        // counts them here instead, on the unstaged path (the work is the same)
+        if (WORK) {
+            drain_warp_bin<WORK>(d, 5, s_proc, queue, mq, wk);
+            mark(5);
+            drain_warp_bin<WORK>(d, 4, s_proc, queue, mq, wk);
+            mark(4);
+        }
         drain_tile_bin<32, WORK>(d, 3, s_proc, mq, wk);
         mark(3);
         drain_tile_bin<16, WORK>(d, 2, s_proc, mq, wk);
