@@ -235,8 +235,8 @@ void rept_group_destroy(rept_group* g);
  * control block) lives in one statically allocated device array of
  * REPT_NOALLOC_SCRATCH_BYTES (64 MiB) inside this library; every GPU that
  * loads the library holds that array until the process exits.  A problem
- * needs 12 * n_nodes + 224 * n_edges + 700 KiB bytes of it (for example
- * 2^20 nodes and 240,000 edges); larger problems return REPT_E_SCRATCH
+ * needs 12 * n_nodes + 216 * n_edges + 200 KiB bytes of it (for example
+ * 2^20 nodes and 250,000 edges); larger problems return REPT_E_SCRATCH
  * before any device work is enqueued.  c must be at most 4096.
  *
  * Arguments: d_src / d_dst: device arrays of n_edges uint32 endpoints

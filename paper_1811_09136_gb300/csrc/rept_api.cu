@@ -43,9 +43,6 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
     } while (0)
 
 int status_to_code(unsigned st) {
-#ifdef REPT_DEBUG_BOUNDS
-    (void)0;
-#endif
     if (st & kStRange) return REPT_E_RANGE;
     if (st & kStCapacity) return REPT_E_CAPACITY;
     if (st & kStTimeout) return REPT_E_TIMEOUT;
@@ -72,7 +69,6 @@ struct rept_state {
     double* d_local_tmp = nullptr;
     int grid_stream = 0;     // blocks for edge/node-parallel kernels
     int grid_intersect = 0;  // blocks for k_intersect
-    int grid_hub = 0;        // blocks for k_intersect_hub
     size_t device_bytes = 0;
     // REPT_FLAG_PROFILE: event pairs recorded around launches, folded into totals on query
     struct Timed { int kernel; cudaEvent_t start, stop; };
@@ -101,19 +97,6 @@ void dev_free(rept_state* s, void* p, size_t bytes) {
 // most 8 slots per entry, and its successive blocks form a doubling series bounded by twice the
 // last one, so at most 16 slots per stored entry, i.e. 32 slots (8 quads) per stream edge.
 unsigned long long quads_bound(unsigned long long edges) { return 8ull * edges + 64ull; }
-
-// Capacity (keys, a power of two from 4096 to 32768) of the shared-memory copy of a large table in
-// k_intersect_hub: REPT_STAGE_KEYS in the environment, else kStageKeys.  Counts do not depend on it.
-uint32_t stage_keys_setting() {
-    const char* e = std::getenv("REPT_STAGE_KEYS");
-    if (e) {
-        const long v = std::strtol(e, nullptr, 10);
-        if (v >= 4096 && v <= 32768 && (v & (v - 1)) == 0) return (uint32_t)v;
-    }
-    return kStageKeys;
-}
-
-size_t hub_smem_bytes(const StreamDev& d) { return ((d.c * 8u + 15u) & ~15u) + (size_t)d.stage_keys * 4u; }
 
 int grow_pool(rept_state* s, unsigned long long min_quads, cudaStream_t st) {
     unsigned long long want = std::max(min_quads, 2ull * s->d.pool_quads);
@@ -148,16 +131,13 @@ int ensure_batch_scratch(rept_state* s, unsigned long long n, cudaStream_t st) {
     dev_free(s, s->d.big, 2 * old * sizeof(uint32_t));
     dev_free(s, s->d.rec, old * sizeof(WorkItem));
     dev_free(s, s->d.srec, old * sizeof(WorkItem));
-    dev_free(s, s->d.runs, old * sizeof(uint2));
     s->d.touched = s->d.grow_rel = s->d.big = nullptr;
     s->d.rec = s->d.srec = nullptr;
-    s->d.runs = nullptr;
     int rc = dev_alloc(s, (void**)&s->d.touched, 2 * n * sizeof(uint32_t));
     if (!rc) rc = dev_alloc(s, (void**)&s->d.grow_rel, 2 * n * sizeof(uint32_t));
     if (!rc) rc = dev_alloc(s, (void**)&s->d.big, 2 * n * sizeof(uint32_t));
     if (!rc) rc = dev_alloc(s, (void**)&s->d.rec, n * sizeof(WorkItem));
     if (!rc) rc = dev_alloc(s, (void**)&s->d.srec, n * sizeof(WorkItem));
-    if (!rc) rc = dev_alloc(s, (void**)&s->d.runs, n * sizeof(uint2));
     if (rc) return rc;
     s->max_batch = n;
     s->d.big_cap = 2 * n;
@@ -246,14 +226,10 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
     const unsigned long long want_i = (n * 8 + 255) / 256;  // work is claimed dynamically; >= 1 block
     const int grid_i = (int)std::min<unsigned long long>(want_i, (unsigned long long)s->grid_intersect);
     const size_t smem = s->cfg.c * sizeof(unsigned long long);
-    const size_t hub_smem = hub_smem_bytes(s->d);
     if (s->cfg.flags & REPT_FLAG_WORK_COUNTERS)
         rc = timed_launch(s, REPT_K_INTERSECT, st, [&] { k_intersect<true><<<grid_i, 256, smem, st>>>(s->d, b); });
     else
-        rc = timed_launch(s, REPT_K_INTERSECT, st, [&] {
-            k_intersect_hub<false><<<s->grid_hub, 256, hub_smem, st>>>(s->d, b);
-            k_intersect<false><<<grid_i, 256, smem, st>>>(s->d, b);
-        }, 2);
+        rc = timed_launch(s, REPT_K_INTERSECT, st, [&] { k_intersect<false><<<grid_i, 256, smem, st>>>(s->d, b); });
     if (rc) return rc;
     s->next_t += n;
     return REPT_OK;
@@ -262,11 +238,6 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
 int sync_status(rept_state* s, cudaStream_t st) {
     int rc = read_ctrl(s, st);
     if (rc) return rc;
-#ifdef REPT_DEBUG_BOUNDS
-    if (s->h_ctrl->dbg[3])
-        std::fprintf(stderr, "rept bounds check %llu failed: index %llu bound %llu (%llu times)\n",
-                     s->h_ctrl->dbg[0], s->h_ctrl->dbg[1], s->h_ctrl->dbg[2], s->h_ctrl->dbg[3]);
-#endif
     return status_to_code(s->h_ctrl->status);
 }
 
@@ -308,20 +279,6 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
                                                       cfg->c * sizeof(unsigned long long)) != cudaSuccess)
         return fail(REPT_E_CUDA);
     s->grid_intersect = s->sm_count * std::max(per_sm, 1);
-    {
-        StreamDev probe{};
-        probe.c = cfg->c;
-        probe.stage_keys = stage_keys_setting();
-        const size_t hs = hub_smem_bytes(probe);
-        // the limit is a property of the kernel, shared by every handle: allow the largest any handle uses
-        const int hub_max = (int)(((kMaxProcessors * 8u + 15u) & ~15u) + 32768u * 4u);
-        int hub_per_sm = 0;
-        if (cudaFuncSetAttribute(k_intersect_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hub_max) !=
-                cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&hub_per_sm, k_intersect_hub<false>, 256, hs) != cudaSuccess)
-            return fail(REPT_E_CUDA);
-        s->grid_hub = s->sm_count * std::max(hub_per_sm, 1);
-    }
     s->grid_stream = s->sm_count * 8;
     s->groups = cfg->c <= cfg->m ? 1u : cfg->c / cfg->m;
     const uint32_t n = cfg->n_nodes;
@@ -333,7 +290,6 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     d.seed = cfg->seed;
     d.fm = make_fastmod(cfg->m);
     d.tile_max = cfg->tile_max == 0 ? 32u : cfg->tile_max;
-    d.stage_keys = stage_keys_setting();
     const unsigned long long mb = cfg->max_batch ? cfg->max_batch : (1ull << 20);
     unsigned long long quads = cfg->expected_edges ? quads_bound(cfg->expected_edges) : quads_bound(mb);
     if (quads > 0xFFFFFFFFull) quads = 0xFFFFFFFFull;
@@ -535,7 +491,6 @@ void rept_destroy(rept_state* s) {
     cudaFree(d.big);
     cudaFree(d.rec);
     cudaFree(d.srec);
-    cudaFree(d.runs);
     cudaFree(d.hist);
     cudaFree(s->stage_src);
     cudaFree(s->stage_dst);

@@ -34,23 +34,12 @@ constexpr uint32_t kNoGrow = 0xFFFFFFFFu;
 constexpr uint32_t kMaxProcessors = 4096;  // per-block tau^(i) histogram lives in shared memory
 // Number of k_intersect work classes (see bin_of_cnt).
 constexpr int kBins = 6;
-// Within a class, work items are ordered by a hash of the larger endpoint, so that the edges
-// probing the same large table run back to back: 13 bits for the four tile classes (the table is
-// then found in L2), 16 bits for the two warp classes, whose runs of equal keys k_intersect_hub
-// serves from a copy of the table in shared memory.
-__host__ __device__ __forceinline__ uint32_t class_key_bits(int cls) { return cls < 4 ? 13u : 16u; }
-__host__ __device__ __forceinline__ uint32_t class_key_base(int cls) {
-    return cls < 4 ? (uint32_t)cls << 13 : (4u << 13) + ((uint32_t)(cls - 4) << 16);
-}
-constexpr uint32_t kHubKeyBase = 4u << 13;                      // first key of the warp classes
-constexpr uint32_t kSortBuckets = (4u << 13) + (2u << 16);      // 163,840 keys
-constexpr uint32_t kNoKey = 0xFFFFFFFFu;
-constexpr uint32_t kRunMax = 64;        // items per run of k_intersect_hub
-constexpr uint32_t kStageKeys = 16384;  // default: largest table k_intersect_hub copies to shared memory (64 KB)
-
-__host__ __device__ __forceinline__ uint32_t sort_key(int cls, uint32_t l) {
-    return class_key_base(cls) + ((l * 0x9E3779B1u) >> (32u - class_key_bits(cls)));
-}
+// Within a class, work items are ordered by a hash of the larger endpoint (kKeyBits bits), so that
+// the edges probing the same large table run back to back and find it in L2.
+constexpr int kKeyBits = 13;
+constexpr uint32_t kKeyBuckets = 1u << kKeyBits;
+constexpr uint32_t kSortBuckets = kBins * kKeyBuckets;
+constexpr uint16_t kNoKey = 0xFFFFu;
 
 // status bits (sticky)
 constexpr unsigned kStRange = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeout = 8u;
@@ -110,9 +99,6 @@ struct Ctrl {
     unsigned long long bin_start[kBins];
     unsigned long long bin_count[kBins];
     unsigned long long bin_next[kBins];
-    unsigned long long n_runs;    // runs of equal warp-class keys (k_intersect_hub), at most kRunMax items
-    unsigned long long run_next;  // claim cursor over the runs
-    unsigned long long dbg[4];  // REPT_DEBUG_BOUNDS builds: first failed check {where, index, bound, count}
     unsigned long long n_big;   // nodes whose table (32..2048 slots) k_rehash_big moves, a warp each
     unsigned long long n_huge;  // nodes whose table (>= 4096 slots) k_rehash_huge moves, a block each
     unsigned long long huge_next;
@@ -126,7 +112,7 @@ struct __align__(16) WorkItem {
     uint32_t t;      // stream index of the edge
     uint32_t lgs;    // log2 table sizes: smaller | larger << 8
     uint32_t cnt_s;  // entries of the smaller endpoint
-    uint32_t key;    // sort_key(work class, l), or kNoKey
+    uint32_t key;    // work class * kKeyBuckets + hash of l, or kNoKey
 };
 
 // Everything a kernel needs to know about one stream's state.
@@ -135,7 +121,6 @@ struct StreamDev {
     uint64_t seed;
     FastMod fm;         // x mod m
     uint32_t tile_max;  // edges whose smaller endpoint has more entries get a warp (4, 8, 16 or 32)
-    uint32_t stage_keys;  // largest larger-endpoint table k_intersect_hub copies to shared memory
     uint2* meta;
     uint2* pool;
     unsigned long long pool_quads;
@@ -147,7 +132,6 @@ struct StreamDev {
     struct WorkItem* rec;   // [max_batch] work record of each edge (key kNoKey if it closes no wedge)
     struct WorkItem* srec;  // [max_batch] the records of edges that can close wedges, sorted by key
     uint32_t* hist;         // [kSortBuckets] counts, then cursors, of the counting sort by key
-    uint2* runs;            // [max_batch] runs {first item, items} of the warp classes
     uint32_t* big;      // [big_cap] touched-list indices of nodes with a large table to move: the
                         // k_rehash_big list from the front, the k_rehash_huge list from the back
     unsigned long long big_cap;
@@ -161,23 +145,6 @@ struct BatchDev {
     unsigned long long n;
     unsigned long long t0;  // stream index of src[0], dst[0]
 };
-
-// Bounds checks of the REPT_DEBUG_BOUNDS build: a failed check records {where, index, bound} once and
-// counts, and the caller skips the access.  Release builds compile them away.
-#ifdef REPT_DEBUG_BOUNDS
-__device__ __forceinline__ bool dbg_ok(Ctrl* c, unsigned where, unsigned long long idx, unsigned long long bound) {
-    if (idx < bound) return true;
-    if (atomicAdd(&c->dbg[3], 1ull) == 0ull) {
-        c->dbg[0] = where;
-        c->dbg[1] = idx;
-        c->dbg[2] = bound;
-    }
-    return false;
-}
-#define REPT_CHECK(c, where, idx, bound) dbg_ok((c), (where), (idx), (bound))
-#else
-#define REPT_CHECK(c, where, idx, bound) true
-#endif
 
 // One output step of SplitMix64 from state x (Steele, Lea, Flood 2014).
 __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {

@@ -245,7 +245,7 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
                 it.t = (uint32_t)(b.t0 + e);
                 it.lgs = table_lg(ms.y) | (table_lg(ml.y) << 8);
                 it.cnt_s = ms.y;
-                key = sort_key(bin_of_cnt(ms.y, d.tile_max), it.l);
+                key = (uint32_t)bin_of_cnt(ms.y, d.tile_max) * kKeyBuckets + ((it.l * 0x9E3779B1u) >> (32 - kKeyBits));
             }
         }
         it.key = key;
@@ -262,71 +262,51 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
 
 // Exclusive scan of the counting-sort histogram (one block of 1024 threads): counts become the
 // first position of each key, and the class boundaries are recorded.
-// Exclusive scan over the block of 1024 threads: returns the sum of v over lower threads; *total the sum
-// over all.  `ws` is 32 words of shared memory.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* ws, uint32_t* total) {
+__device__ __forceinline__ void k_sort_scan_body(const StreamDev& d) {
+    constexpr uint32_t kPer = kSortBuckets / 1024;
+    __shared__ uint32_t warp_sum[32];
+    if (d.ctrl->status) return;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
-    uint32_t incl = v;
+    uint32_t local[kPer];
+    uint32_t sum = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < kPer; ++k) {
+        local[k] = d.hist[tid * kPer + k];
+        sum += local[k];
+    }
+    uint32_t incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
         if (lane >= (uint32_t)o) incl += y;
     }
-    if (lane == 31) ws[wid] = incl;
+    if (lane == 31) warp_sum[wid] = incl;
     __syncthreads();
     if (wid == 0) {
-        const uint32_t w = ws[lane];
-        uint32_t wi = w;
+        uint32_t w = warp_sum[lane], wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
             if (lane >= (uint32_t)o) wi += y;
         }
-        ws[lane] = wi - w;
-        if (lane == 31) ws[32] = wi;
+        warp_sum[lane] = wi - w;
     }
     __syncthreads();
-    const uint32_t ex = ws[wid] + incl - v;
-    *total = ws[32];
-    __syncthreads();
-    return ex;
-}
-
-// Exclusive scan of the counting-sort histogram (one block of 1024 threads): counts become the
-// first position of each key and the class boundaries are recorded.  The keys of the warp classes
-// with items become runs of at most kRunMax items for k_intersect_hub.
-__device__ __forceinline__ void k_sort_scan_body(const StreamDev& d) {
-    constexpr uint32_t kPer = kSortBuckets / 1024;
-    __shared__ uint32_t ws[33];
-    if (d.ctrl->status) return;
-    const uint32_t tid = threadIdx.x;
-    uint32_t sum = 0, nsub = 0;
+    uint32_t run = warp_sum[wid] + incl - sum;
+#pragma unroll
     for (uint32_t k = 0; k < kPer; ++k) {
-        const uint32_t key = tid * kPer + k, cnt = d.hist[key];
-        sum += cnt;
-        if (key >= kHubKeyBase) nsub += (cnt + kRunMax - 1) / kRunMax;
-    }
-    uint32_t total = 0, total_runs = 0;
-    uint32_t run = block_exclusive_scan(sum, ws, &total);
-    uint32_t sub = block_exclusive_scan(nsub, ws, &total_runs);
-    for (uint32_t k = 0; k < kPer; ++k) {
-        const uint32_t key = tid * kPer + k, cnt = d.hist[key];
-        for (int c = 0; c < kBins; ++c)
-            if (key == class_key_base(c)) d.ctrl->bin_start[c] = run;
-        if (key >= kHubKeyBase)
-            for (uint32_t o = 0; o < cnt; o += kRunMax) d.runs[sub++] = make_uint2(run + o, min(kRunMax, cnt - o));
+        const uint32_t key = tid * kPer + k;
+        if (key % kKeyBuckets == 0u) d.ctrl->bin_start[key / kKeyBuckets] = run;
         d.hist[key] = run;
-        run += cnt;
+        run += local[k];
     }
     __syncthreads();
-    if (tid == 0) {
-        unsigned long long prev = total;
+    if (tid == 1023) {  // totals: the last thread's running sum is the number of items
+        unsigned long long prev = run;
         for (int c = kBins - 1; c >= 0; --c) {
             d.ctrl->bin_count[c] = prev - d.ctrl->bin_start[c];
             prev = d.ctrl->bin_start[c];
         }
-        d.ctrl->n_runs = total_runs;
-        d.ctrl->run_next = 0ull;
     }
 }
 
@@ -394,7 +374,7 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
             atomicAdd(&s_proc[k * d.m + js], 1ull);
         }
     }
-    if (found && REPT_CHECK(d.ctrl, 6, (unsigned long long)max(w, max(s, l)), d.n_nodes)) {
+    if (found) {
         atomicAdd(&d.local[w], (unsigned long long)found);
         atomicAdd(&d.local[s], (unsigned long long)found);
         atomicAdd(&d.local[l], (unsigned long long)found);
@@ -430,7 +410,7 @@ __device__ __forceinline__ void mq_push(const StreamDev& d, MatchQueue& q, bool 
                                         uint32_t w, unsigned long long* s_proc, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, has);
-    if (has && REPT_CHECK(d.ctrl, 7, q.n + __popc(mask & ((1u << lane) - 1u)), kMatchQ)) {
+    if (has) {
         const uint32_t i = q.n + __popc(mask & ((1u << lane) - 1u));
         q.s[i] = s;
         q.l[i] = l;
@@ -475,8 +455,7 @@ constexpr int kProbesPerLane = REPT_PROBES_PER_LANE;  // probes each lane keeps 
 
 template <bool WORK>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, unsigned long long* s_proc,
-                                               uint32_t* queue, MatchQueue& mq, Work& wk,
-                                               const uint32_t* staged = nullptr) {
+                                               uint32_t* queue, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const uint32_t lg_l = x.lgs >> 8, n_s = x.cnt_s;
     const unsigned long long base_l = 4ull * x.off_l;
@@ -490,22 +469,19 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
         for (uint32_t half = 0; half < 2; ++half) {
             const uint32_t jj = j0 + 64u * half + 2u * lane;
             uint4 q = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-            if (jj < n_s && REPT_CHECK(d.ctrl, 4, 4ull * x.off_s + (1ull << (x.lgs & 0xFFu)) + jj + 1,
-                                       4ull * d.pool_quads))
-                q = list[jj >> 1];
+            if (jj < n_s) q = list[jj >> 1];
             const bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
             const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
-            if (a1 && REPT_CHECK(d.ctrl, 8, n_q + __popc(m1 & below), kQueue)) queue[n_q + __popc(m1 & below)] = q.x;
+            if (a1) queue[n_q + __popc(m1 & below)] = q.x;
             n_q += __popc(m1);
-            if (a2 && REPT_CHECK(d.ctrl, 8, n_q + __popc(m2 & below), kQueue)) queue[n_q + __popc(m2 & below)] = q.z;
+            if (a2) queue[n_q + __popc(m2 & below)] = q.z;
             n_q += __popc(m2);
         }
         __syncwarp();
         // kProbesPerLane queued neighbours per lane: all their home buckets are loaded before any is
         // examined, then the stream indices of the hits
-        // the larger endpoint's keys: a copy in shared memory when the caller staged one
         const uint32_t* keys_l = reinterpret_cast<const uint32_t*>(d.pool + base_l);
-        const uint4* buckets_l = reinterpret_cast<const uint4*>(staged ? staged : keys_l);
+        const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
         const uint32_t cap_l = 1u << lg_l;
         for (uint32_t k0 = 0; k0 < n_q; k0 += 32u * kProbesPerLane) {
             uint32_t w[kProbesPerLane], h[kProbesPerLane], r[kProbesPerLane];
@@ -516,9 +492,7 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
                 w[p] = v ? queue[k0 + 32u * p + lane] : kEmptyId;
                 h[p] = home_slot(w[p], lg_l);
                 bk[p] = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-                if (v && REPT_CHECK(d.ctrl, 3, h[p], staged ? d.stage_keys : cap_l) &&
-                    REPT_CHECK(d.ctrl, 4, 4ull * x.off_l + cap_l, 4ull * d.pool_quads))
-                    bk[p] = buckets_l[h[p] >> 2];
+                if (v) bk[p] = __ldg(&buckets_l[h[p] >> 2]);
             }
 #pragma unroll
             for (int p = 0; p < kProbesPerLane; ++p) {
@@ -615,14 +589,10 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
                 p0 = p1;
             }
         };
-        // classes 4 and 5 (a warp per edge) are served by k_intersect_hub; the work-counting pass
-        // counts them here instead, on the unstaged path (the work is the same)
-        if (WORK) {
-            drain_warp_bin<WORK>(d, 5, s_proc, queue, mq, wk);
-            mark(5);
-            drain_warp_bin<WORK>(d, 4, s_proc, queue, mq, wk);
-            mark(4);
-        }
+        drain_warp_bin<WORK>(d, 5, s_proc, queue, mq, wk);
+        mark(5);
+        drain_warp_bin<WORK>(d, 4, s_proc, queue, mq, wk);
+        mark(4);
         drain_tile_bin<32, WORK>(d, 3, s_proc, mq, wk);
         mark(3);
         drain_tile_bin<16, WORK>(d, 2, s_proc, mq, wk);
@@ -651,89 +621,6 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
             atomicAdd(&d.ctrl->probe_slots, wk.pslots);
             atomicAdd(&d.ctrl->wedges, wk.wedges);
             atomicAdd(&d.ctrl->counted, wk.counted);
-        }
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < d.c; i += blockDim.x)
-        if (s_proc[i]) atomicAdd(&d.proc[i], s_proc[i]);
-}
-
-// Edges of the warp classes, one run (at most kRunMax edges with the same sort key, nearly always the
-// same larger endpoint l) at a time per thread block: the block copies l's key table into shared
-// memory once (when it has at most kStageKeys slots) and its warps probe the copy; a stream index is
-// read from global memory only for a hit.  Runs are taken largest class first.
-// Dynamic shared memory: c uint64 counters (tau^(i)), then d.stage_keys keys.
-template <bool WORK>
-__device__ __forceinline__ void k_intersect_hub_body(const StreamDev& d, const BatchDev& b) {
-    extern __shared__ __align__(16) unsigned char hub_smem[];
-    unsigned long long* s_proc = reinterpret_cast<unsigned long long*>(hub_smem);
-    uint32_t* stage = reinterpret_cast<uint32_t*>(hub_smem + ((d.c * 8u + 15u) & ~15u));
-    __shared__ uint32_t s_queue[256 / 32][kQueue];
-    __shared__ uint32_t s_match[256 / 32][3][kMatchQ];
-    __shared__ unsigned long long s_r;
-    __shared__ uint32_t s_next;
-    for (uint32_t i = threadIdx.x; i < d.c; i += blockDim.x) s_proc[i] = 0ull;
-    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    uint32_t* queue = s_queue[wid];
-    MatchQueue mq{s_match[wid][0], s_match[wid][1], s_match[wid][2], 0u};
-    Work wk;
-    const unsigned long long n_runs = d.ctrl->status == 0u ? d.ctrl->n_runs : 0ull;
-    long long t0 = WORK ? clock64() : 0;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            s_r = atomicAdd(&d.ctrl->run_next, 1ull);
-            s_next = 0u;
-        }
-        __syncthreads();
-        const unsigned long long r = s_r;
-        if (r >= n_runs) break;
-        if (!REPT_CHECK(d.ctrl, 1, n_runs - 1 - r, b.n)) break;
-        const uint2 run = d.runs[n_runs - 1 - r];  // the larger class's runs sit at the end
-        if (!REPT_CHECK(d.ctrl, 2, (unsigned long long)run.x + run.y, b.n + 1)) break;
-        const WorkItem x0 = d.srec[run.x];
-        const uint32_t cap0 = 1u << (x0.lgs >> 8);
-        const bool staged = cap0 <= d.stage_keys;
-        if (staged && REPT_CHECK(d.ctrl, 11, 4ull * x0.off_l + cap0, 4ull * d.pool_quads + 1)) {
-            const uint4* src = reinterpret_cast<const uint4*>(d.pool + 4ull * x0.off_l);
-            uint4* dst = reinterpret_cast<uint4*>(stage);
-            for (uint32_t q = threadIdx.x; q < cap0 / 4u; q += blockDim.x) dst[q] = src[q];
-        }
-        __syncthreads();
-        for (;;) {
-            uint32_t i = 0;
-            if (lane == 0) i = atomicAdd(&s_next, 1u);
-            i = __shfl_sync(0xFFFFFFFFu, i, 0);
-            if (i >= run.y) break;
-            const WorkItem x = d.srec[run.x + i];
-            const bool mine = staged && x.l == x0.l && x.off_l == x0.off_l;
-            const unsigned long long p0 = wk.probes;
-            intersect_warp<WORK>(d, x, s_proc, queue, mq, wk, mine ? stage : nullptr);
-            if (WORK) {
-                const long long t1 = clock64();
-                unsigned long long pr = wk.probes - p0;
-                for (int o = 16; o > 0; o >>= 1) pr += __shfl_down_sync(0xFFFFFFFFu, pr, o);
-                const int cls = bin_of_cnt(x.cnt_s, d.tile_max);
-                if (lane == 0) {
-                    atomicAdd(&d.ctrl->class_cycles[cls], (unsigned long long)(t1 - t0));
-                    atomicAdd(&d.ctrl->class_probes[cls], pr);
-                }
-                t0 = t1;
-            }
-        }
-        __syncthreads();  // the copy of l's table is about to be replaced
-    }
-    if (mq.n) mq_flush<WORK>(d, mq, mq.n, s_proc, wk);
-    if (WORK) {
-        unsigned long long v[6] = {wk.entries, wk.slots, wk.probes, wk.pslots, wk.wedges, wk.counted};
-        for (int q = 0; q < 6; ++q)
-            for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xFFFFFFFFu, v[q], o);
-        if (lane == 0) {
-            atomicAdd(&d.ctrl->small_entries, v[0]);
-            atomicAdd(&d.ctrl->small_slots, v[1]);
-            atomicAdd(&d.ctrl->probes, v[2]);
-            atomicAdd(&d.ctrl->probe_slots, v[3]);
-            atomicAdd(&d.ctrl->wedges, v[4]);
-            atomicAdd(&d.ctrl->counted, v[5]);
         }
     }
     __syncthreads();
@@ -1062,24 +949,6 @@ __global__ void k_sort_scatter_multi(const StreamDev* __restrict__ ds, const Bat
 
 template <bool WORK>
 __global__ void __launch_bounds__(256, 8) k_intersect(StreamDev d, BatchDev b) { k_intersect_body<WORK>(d, b); }
-
-template <bool WORK>
-__global__ void __launch_bounds__(256, 2) k_intersect_hub(StreamDev d, BatchDev b) {
-    k_intersect_hub_body<WORK>(d, b);
-}
-
-template <bool WORK>
-__global__ void __launch_bounds__(256, 2) k_intersect_hub_multi(const StreamDev* __restrict__ ds,
-                                                                 const BatchDev* __restrict__ bs) {
-    __shared__ StreamDev sd;
-    __shared__ BatchDev sb;
-    if (threadIdx.x == 0) {
-        sd = ds[blockIdx.y];
-        sb = bs[blockIdx.y];
-    }
-    __syncthreads();
-    k_intersect_hub_body<WORK>(sd, sb);
-}
 
 template <bool WORK>
 __global__ void __launch_bounds__(256, 8) k_intersect_multi(const StreamDev* __restrict__ ds,

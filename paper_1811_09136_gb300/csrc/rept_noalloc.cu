@@ -25,7 +25,7 @@ inline unsigned long long align256(unsigned long long x) { return (x + 255ull) &
 
 // Offsets of the state inside the scratch area for n nodes and E edges.
 struct Layout {
-    unsigned long long meta, add, touched, grow_rel, big, rec, srec, runs, hist, ctrl, pool, end;
+    unsigned long long meta, add, touched, grow_rel, big, rec, srec, hist, ctrl, pool, end;
     unsigned long long pool_quads;
 };
 
@@ -39,7 +39,6 @@ Layout layout_for(unsigned long long n, unsigned long long E) {
     L.big = o;      o = align256(o + 2 * E * sizeof(uint32_t));
     L.rec = o;      o = align256(o + E * sizeof(WorkItem));
     L.srec = o;     o = align256(o + E * sizeof(WorkItem));
-    L.runs = o;     o = align256(o + E * sizeof(uint2));
     L.hist = o;     o = align256(o + kSortBuckets * sizeof(uint32_t));
     L.ctrl = o;     o = align256(o + sizeof(Ctrl));
     // From an empty state every node's block (table plus list) is allocated once, with at most 8
@@ -100,7 +99,6 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
     d.seed = seed;
     d.fm = make_fastmod(m);
     d.tile_max = 32u;
-    d.stage_keys = kStageKeys;
     d.meta = reinterpret_cast<uint2*>(sc + L.meta);
     d.add = reinterpret_cast<uint32_t*>(sc + L.add);
     d.touched = reinterpret_cast<uint32_t*>(sc + L.touched);
@@ -109,7 +107,6 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
     d.big_cap = 2 * (n_edges ? n_edges : 1);
     d.rec = reinterpret_cast<WorkItem*>(sc + L.rec);
     d.srec = reinterpret_cast<WorkItem*>(sc + L.srec);
-    d.runs = reinterpret_cast<uint2*>(sc + L.runs);
     d.hist = reinterpret_cast<uint32_t*>(sc + L.hist);
     d.ctrl = reinterpret_cast<Ctrl*>(sc + L.ctrl);
     d.pool = reinterpret_cast<uint2*>(sc + L.pool);
@@ -143,10 +140,6 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
         k_sort_scatter<<<grid, threads, 0, st>>>(d, b);
         const unsigned long long want_i = (n_edges * 8 + 255) / 256;
         const int grid_i = (int)(want_i < (unsigned long long)sms * 4 ? want_i : (unsigned long long)sms * 4);
-        const size_t hub_smem = ((c * 8u + 15u) & ~15u) + (size_t)kStageKeys * 4u;
-        NA_CUDA(cudaFuncSetAttribute(k_intersect_hub<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(((kMaxProcessors * 8u + 15u) & ~15u) + 32768u * 4u)));
-        k_intersect_hub<false><<<sms * 2, 256, hub_smem, st>>>(d, b);
         k_intersect<false><<<grid_i, 256, c * sizeof(unsigned long long), st>>>(d, b);
         NA_CUDA(cudaPeekAtLastError());
     }
