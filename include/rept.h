@@ -161,6 +161,18 @@ int rept_estimates(rept_state* s, double* h_global, double* d_local, void* strea
 int rept_estimates_host(rept_state* s, double* h_global, double* h_local, void* stream);
 
 /*
+ * rept_estimates_async: enqueue, without waiting, the computation of tau_hat
+ * (as in rept_estimates) and copies to host memory of tau_hat (h_global, one
+ * double), the c counters tau^(i) (h_proc, or NULL) and the handle's status
+ * word (h_status: 0 when no device error was recorded, else nonzero; the
+ * next synchronising call returns the matching REPT_E_* code).  The host
+ * buffers should be pinned for the copies to be asynchronous; their contents
+ * are valid once `stream` has reached this point (record an event after the
+ * call and wait on it).
+ */
+int rept_estimates_async(rept_state* s, double* h_global, uint64_t* h_proc, uint32_t* h_status, void* stream);
+
+/*
  * rept_counts: the integer counters.  h_proc: host array of c uint64
  * (tau^(i), processor i = k*m + j), or NULL.  d_local: device array of
  * n_nodes uint64 receiving sum_i tau_v^(i) over all processors, or NULL.

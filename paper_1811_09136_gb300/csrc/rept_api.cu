@@ -402,6 +402,21 @@ int rept_estimates(rept_state* s, double* h_global, double* d_local, void* strea
     return rc;
 }
 
+int rept_estimates_async(rept_state* s, double* h_global, uint64_t* h_proc, uint32_t* h_status, void* stream) {
+    if (!s || !h_global || !h_status) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    const double f = estimate_factor(s->cfg);
+    int rc = timed_launch(s, REPT_K_ESTIMATE, st,
+                          [&] { k_global_estimate<<<1, 256, 0, st>>>(s->d.proc, s->cfg.c, f, s->d_global); });
+    if (rc) return rc;
+    REPT_CUDA(cudaMemcpyAsync(h_global, s->d_global, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (h_proc)
+        REPT_CUDA(cudaMemcpyAsync(h_proc, s->d.proc, (size_t)s->cfg.c * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                  st));
+    REPT_CUDA(cudaMemcpyAsync(h_status, &s->d.ctrl->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    return REPT_OK;
+}
+
 int rept_estimates_host(rept_state* s, double* h_global, double* h_local, void* stream) {
     if (!s || !h_global) return REPT_E_INVAL;
     cudaStream_t st = as_stream(stream);

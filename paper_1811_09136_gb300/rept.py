@@ -74,6 +74,7 @@ def load():
             "rept_ingest_host": (ctypes.c_int, [_vp, _vp, _vp, _u64, _u64, _vp]),
             "rept_estimates": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
             "rept_estimates_host": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
+            "rept_estimates_async": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
             "rept_counts": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "rept_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats), _vp]),
             "rept_sync": (ctypes.c_int, [_vp, _vp]),
@@ -203,6 +204,14 @@ class ReptStream:
         _check(self._lib.rept_estimates_host(self._h, ctypes.byref(g), ctypes.c_void_p(out.ctypes.data),
                                              _cur_stream(stream)), "rept_estimates_host")
         return g.value, out
+
+    def estimates_async(self, h_global: np.ndarray, h_proc: np.ndarray, h_status: np.ndarray, stream=None):
+        """Enqueue tau_hat, tau^(i) and the status word for copy into the given (pinned) numpy arrays
+        of 1 float64, c uint64 and 1 uint32; they are valid once the stream passes this point."""
+        _check(self._lib.rept_estimates_async(self._h, ctypes.c_void_p(h_global.ctypes.data),
+                                              ctypes.c_void_p(h_proc.ctypes.data),
+                                              ctypes.c_void_p(h_status.ctypes.data), _cur_stream(stream)),
+               "rept_estimates_async")
 
     def counts(self, stream=None, allow_error: bool = False):
         """(tau^(i) as numpy uint64 [c], sum_i tau_v^(i) as an int64 CUDA tensor [n_nodes]).

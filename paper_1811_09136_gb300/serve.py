@@ -49,6 +49,9 @@ class _Live:
     fed: int = 0
     bytes: int = 0
     ready: object = None       # CUDA event: edges uploaded
+    waited: bool = False       # the compute stream already waits for the upload
+    out: tuple = ()            # pinned result buffers (tau_hat, tau^(i), status)
+    done_ev: object = None     # CUDA event: results copied to the host
 
 
 @dataclass
@@ -78,8 +81,14 @@ def poisson_arrivals(n: int, rate: float, seed: int = 5) -> np.ndarray:
 
 
 def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None = None,
-          graph: bool = True, keep_local: bool = False, clock=time.perf_counter) -> ServeReport:
-    """Run the trace.  Requests must be sorted by arrival time."""
+          graph: bool = False, keep_local: bool = False, clock=time.perf_counter,
+          free_batch: int = 16) -> ServeReport:
+    """Run the trace.  Requests must be sorted by arrival time.
+
+    A finished stream's estimates are requested asynchronously (rept_estimates_async into pinned
+    memory, completion seen through a CUDA event), so the next round starts at once; finished
+    handles are released `free_batch` at a time, or earlier when admission needs the memory,
+    because releasing device memory waits for the whole device."""
     import torch
 
     torch.cuda.synchronize()
@@ -90,25 +99,65 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
     pending = list(requests)
     pending.reverse()          # pop() from the end = earliest arrival
     live: list[_Live] = []
+    completing: list[_Live] = []
+    graveyard: list[_Live] = []
     used = 0
     rep = ServeReport()
+    pinned: dict[int, tuple] = {}
+
+    def release_graveyard():
+        nonlocal used
+        for x in graveyard:
+            x.handle.close()
+            used -= x.bytes
+        graveyard.clear()
+
+    def host_edges(r):
+        key = id(r.stream)
+        if key not in pinned:
+            pinned[key] = (torch.from_numpy(r.stream.src.view(np.int32)).pin_memory(),
+                           torch.from_numpy(r.stream.dst.view(np.int32)).pin_memory())
+        return pinned[key]
+
     t0 = clock()
-    while pending or live:
+    while pending or live or completing:
         now = clock() - t0
+        # results whose copies have landed
+        for x in [x for x in completing if x.done_ev.query()]:
+            r = x.req
+            g, proc, status = x.out
+            if int(status[0]) != 0:
+                x.handle.sync()  # raises the handle's REPT_E_* error
+            r.tau_hat = float(g[0])
+            r.proc = proc.copy()
+            if keep_local:
+                _, local = x.handle.counts()
+                r.local = local.cpu().numpy().view(np.uint64)
+            r.done = clock() - t0
+            rep.edges += len(r.stream)
+            rep.requests.append(r)
+            completing.remove(x)
+            graveyard.append(x)
+        if len(graveyard) >= free_batch:
+            release_graveyard()
         # admission: arrived, a slot free, state fits the remaining budget (FIFO, no overtaking)
         while pending and pending[-1].arrival <= now and len(live) < max_live:
             r = pending[-1]
             need = batched._state_bytes(r.stream.n_nodes, len(r.stream), min(r.chunk, len(r.stream))) \
                 + 8 * len(r.stream)
-            if live and used + need > budget:
+            if (live or completing) and used + need > budget:
+                if graveyard:
+                    release_graveyard()
+                    continue
                 break
             pending.pop()
             # state set-up and the edge upload go on the copy stream, next to the running rounds
             h = rept.ReptStream(r.stream.n_nodes, r.m, r.c, r.seed, expected_edges=len(r.stream),
                                 max_batch=min(r.chunk, max(1, len(r.stream))), stream=copy_stream)
+            hsrc, hdst = host_edges(r)
             with torch.cuda.stream(copy_stream):
-                src = torch.from_numpy(r.stream.src.view(np.int32)).pin_memory().to("cuda", non_blocking=True)
-                dst = torch.from_numpy(r.stream.dst.view(np.int32)).pin_memory().to("cuda", non_blocking=True)
+                src = hsrc.to("cuda", non_blocking=True)
+                dst = hdst.to("cuda", non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(copy_stream)
             src.record_stream(compute)
@@ -117,43 +166,43 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
             live.append(_Live(r, h, src, dst, bytes=need, ready=ev))
             used += need
         rep.max_live = max(rep.max_live, len(live))
-        ready = [x for x in live if x.ready.query()]
+        ready = [x for x in live if x.waited or x.ready.query()]
         if not ready:
-            if not live and pending:
-                # idle until the next arrival
+            if live:
+                live[0].ready.synchronize()
+            elif completing:
+                completing[0].done_ev.synchronize()
+            elif pending:
                 wait = pending[-1].arrival - (clock() - t0)
                 if wait > 0:
-                    time.sleep(min(wait, 0.01))
-            elif live:
-                live[0].ready.synchronize()
+                    time.sleep(min(wait, 0.002))
             continue
         # one round: every ready stream gets its next chunk, all in one group launch sequence
         hs, a, b = [], [], []
         for x in ready:
+            if not x.waited:
+                compute.wait_event(x.ready)
+                x.waited = True
             n = min(x.req.chunk, len(x.req.stream) - x.fed)
-            compute.wait_event(x.ready)
             hs.append(x.handle)
             a.append(x.src[x.fed:x.fed + n])
             b.append(x.dst[x.fed:x.fed + n])
             x.fed += n
         group.ingest(hs, a, b)
         rep.rounds += 1
-        finished = [x for x in ready if x.fed >= len(x.req.stream)]
-        for x in finished:
-            r = x.req
-            r.tau_hat, _ = x.handle.estimates(local=False)      # synchronises the stream
-            proc, local = x.handle.counts()
-            r.proc = proc
-            if keep_local:
-                r.local = local.cpu().numpy().view(np.uint64)
-            r.done = clock() - t0
-            rep.edges += len(r.stream)
-            rep.requests.append(r)
-            x.handle.close()
-            used -= x.bytes
+        for x in [x for x in ready if x.fed >= len(x.req.stream)]:
+            x.out = (torch.empty(1, dtype=torch.float64).pin_memory().numpy(),
+                     torch.empty(x.req.c, dtype=torch.int64).pin_memory().numpy().view(np.uint64),
+                     torch.empty(1, dtype=torch.int32).pin_memory().numpy().view(np.uint32))
+            x.handle.estimates_async(*x.out)
+            x.done_ev = torch.cuda.Event()
+            x.done_ev.record(compute)
+            x.src = x.dst = None
             live.remove(x)
+            completing.append(x)
     torch.cuda.synchronize()
     rep.makespan = clock() - t0
+    release_graveyard()
     group.close()
     rep.requests.sort(key=lambda r: r.rid)
     return rep
