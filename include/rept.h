@@ -122,6 +122,14 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out);
 int rept_reset(rept_state* s, void* stream);
 
 /*
+ * rept_reset_async: as rept_reset, without waiting, and the next stream uses
+ * hash seed `seed` (s_0): the whole adjacency pool is cleared (not only its
+ * used part) and everything is enqueued on `stream`.  For servers that reuse
+ * a handle for the next stream of the same shape.
+ */
+int rept_reset_async(rept_state* s, uint64_t seed, void* stream);
+
+/*
  * rept_ingest_batch: append n edges (d_src[t], d_dst[t]), t < n, to the
  * stream and process them exactly as Algorithm 1 would, one edge after the
  * other: every edge first closes the wedges of edges that arrived before it

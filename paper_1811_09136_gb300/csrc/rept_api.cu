@@ -337,6 +337,23 @@ int rept_reset(rept_state* s, void* stream) {
     return REPT_OK;
 }
 
+int rept_reset_async(rept_state* s, uint64_t seed, void* stream) {
+    if (!s) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    StreamDev& d = s->d;
+    s->cfg.seed = seed;
+    d.seed = seed;
+    const size_t n = d.n_nodes;
+    REPT_CUDA(cudaMemsetAsync(d.pool, 0xFF, d.pool_quads * 32ull, st));
+    REPT_CUDA(cudaMemsetAsync(d.meta, 0, n * sizeof(uint2), st));
+    REPT_CUDA(cudaMemsetAsync(d.local, 0, n * sizeof(unsigned long long), st));
+    REPT_CUDA(cudaMemsetAsync(d.proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
+    REPT_CUDA(cudaMemsetAsync(d.add, 0, n * sizeof(uint32_t), st));
+    REPT_CUDA(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), st));
+    s->next_t = 0;
+    return REPT_OK;
+}
+
 int rept_ingest_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, uint64_t n, void* stream) {
     if (!s) return REPT_E_INVAL;
     if (n == 0) return REPT_OK;

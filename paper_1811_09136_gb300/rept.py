@@ -70,6 +70,7 @@ def load():
         sig = {
             "rept_create": (ctypes.c_int, [ctypes.POINTER(Config), _vp, ctypes.POINTER(_vp)]),
             "rept_reset": (ctypes.c_int, [_vp, _vp]),
+            "rept_reset_async": (ctypes.c_int, [_vp, _u64, _vp]),
             "rept_ingest_batch": (ctypes.c_int, [_vp, _vp, _vp, _u64, _vp]),
             "rept_ingest_host": (ctypes.c_int, [_vp, _vp, _vp, _u64, _u64, _vp]),
             "rept_estimates": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
@@ -169,6 +170,13 @@ class ReptStream:
     # ------------------------------------------------------------------
     def reset(self, stream=None):
         _check(self._lib.rept_reset(self._h, _cur_stream(stream)), "rept_reset")
+
+    def reset_async(self, seed: int | None = None, stream=None):
+        """Clear the whole state without waiting (enqueued on `stream`); the next stream uses hash
+        seed `seed` (default: unchanged)."""
+        if seed is not None:
+            self.seed = int(seed)
+        _check(self._lib.rept_reset_async(self._h, self.seed, _cur_stream(stream)), "rept_reset_async")
 
     def ingest(self, src, dst, stream=None):
         """Append device edges (torch int32/uint32 CUDA tensors) as one batch (asynchronous)."""

@@ -86,9 +86,10 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
     """Run the trace.  Requests must be sorted by arrival time.
 
     A finished stream's estimates are requested asynchronously (rept_estimates_async into pinned
-    memory, completion seen through a CUDA event), so the next round starts at once; finished
-    handles are released `free_batch` at a time, or earlier when admission needs the memory,
-    because releasing device memory waits for the whole device."""
+    memory, completion seen through a CUDA event), so the next round starts at once.  Finished
+    handles are kept and reused (rept_reset_async) by later streams of the same shape; they are
+    destroyed only when admission needs their memory, because releasing device memory waits for
+    the whole device."""
     import torch
 
     torch.cuda.synchronize()
@@ -104,13 +105,25 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
     used = 0
     rep = ServeReport()
     pinned: dict[int, tuple] = {}
+    spare: dict[tuple, list] = {}   # finished handles kept for reuse, by shape
+
+    def shape(r):
+        return (r.stream.n_nodes, r.m, r.c, len(r.stream), min(r.chunk, max(1, len(r.stream))))
 
     def release_graveyard():
-        nonlocal used
+        # finished handles become spares for a later stream of the same shape (their memory stays
+        # counted); spares are destroyed only when admission needs the memory
         for x in graveyard:
-            x.handle.close()
-            used -= x.bytes
+            spare.setdefault(shape(x.req), []).append(x)
         graveyard.clear()
+
+    def destroy_spares():
+        nonlocal used
+        for lst in spare.values():
+            for x in lst:
+                x.handle.close()
+                used -= x.bytes
+        spare.clear()
 
     def host_edges(r):
         key = id(r.stream)
@@ -145,15 +158,25 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
             r = pending[-1]
             need = batched._state_bytes(r.stream.n_nodes, len(r.stream), min(r.chunk, len(r.stream))) \
                 + 8 * len(r.stream)
-            if (live or completing) and used + need > budget:
-                if graveyard:
-                    release_graveyard()
-                    continue
-                break
-            pending.pop()
-            # state set-up and the edge upload go on the copy stream, next to the running rounds
-            h = rept.ReptStream(r.stream.n_nodes, r.m, r.c, r.seed, expected_edges=len(r.stream),
-                                max_batch=min(r.chunk, max(1, len(r.stream))), stream=copy_stream)
+            reuse = spare.get(shape(r))
+            if reuse:
+                pending.pop()
+                old = reuse.pop()
+                h = old.handle
+                need = old.bytes
+                used -= old.bytes
+                h.reset_async(seed=r.seed, stream=copy_stream)
+            else:
+                if (live or completing or spare) and used + need > budget:
+                    if graveyard or spare:
+                        release_graveyard()
+                        destroy_spares()
+                        continue
+                    break
+                pending.pop()
+                # state set-up and the edge upload go on the copy stream, next to the running rounds
+                h = rept.ReptStream(r.stream.n_nodes, r.m, r.c, r.seed, expected_edges=len(r.stream),
+                                    max_batch=min(r.chunk, max(1, len(r.stream))), stream=copy_stream)
             hsrc, hdst = host_edges(r)
             with torch.cuda.stream(copy_stream):
                 src = hsrc.to("cuda", non_blocking=True)
@@ -203,6 +226,7 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
     torch.cuda.synchronize()
     rep.makespan = clock() - t0
     release_graveyard()
+    destroy_spares()
     group.close()
     rep.requests.sort(key=lambda r: r.rid)
     return rep

@@ -42,3 +42,18 @@ def test_each_result_is_the_same_alone_and_in_the_mix(max_live, budget):
         assert r.done >= r.admitted >= r.arrival
     s = rep.summary()
     assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
+
+
+@pytest.mark.gpu
+def test_reused_handles_give_the_same_results():
+    """Requests of the same shape reuse a finished handle (rept_reset_async with the new seed)."""
+    specs = batched.mix_specs(2, seed=55, n_min=500, n_max=3000, epn=(4.0, 8.0))
+    streams = batched.generate_all(specs, processes=1)
+    arr = serve.poisson_arrivals(10, 50.0, seed=3)
+    reqs = [serve.Request(i, float(arr[i]), streams[i % 2], specs[i % 2].m, specs[i % 2].m, 500 + i, chunk=1 << 11)
+            for i in range(10)]
+    rep = serve.serve(reqs, max_live=2, keep_local=True)
+    for r in rep.requests:
+        g, proc, local = serve.count_alone(r)
+        assert np.array_equal(r.proc, proc) and np.array_equal(r.local, local)
+        assert abs(r.tau_hat - g) <= 1e-12 * max(abs(g), 1.0)
