@@ -107,8 +107,13 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
     pinned: dict[int, tuple] = {}
     spare: dict[tuple, list] = {}   # finished handles kept for reuse, by shape
 
+    def feed(r):
+        # edges fed per round: the request's chunk, raised for long streams so that a stream needs at
+        # most about 256 rounds, and never above 2^20
+        return min(max(1, len(r.stream)), max(r.chunk, min(1 << 20, len(r.stream) // 256)))
+
     def shape(r):
-        return (r.stream.n_nodes, r.m, r.c, len(r.stream), min(r.chunk, max(1, len(r.stream))))
+        return (r.stream.n_nodes, r.m, r.c, len(r.stream), feed(r))
 
     def release_graveyard():
         # finished handles become spares for a later stream of the same shape (their memory stays
@@ -156,8 +161,7 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
         # admission: arrived, a slot free, state fits the remaining budget (FIFO, no overtaking)
         while pending and pending[-1].arrival <= now and len(live) < max_live:
             r = pending[-1]
-            need = batched._state_bytes(r.stream.n_nodes, len(r.stream), min(r.chunk, len(r.stream))) \
-                + 8 * len(r.stream)
+            need = batched._state_bytes(r.stream.n_nodes, len(r.stream), feed(r)) + 8 * len(r.stream)
             reuse = spare.get(shape(r))
             if reuse:
                 pending.pop()
@@ -176,7 +180,7 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
                 pending.pop()
                 # state set-up and the edge upload go on the copy stream, next to the running rounds
                 h = rept.ReptStream(r.stream.n_nodes, r.m, r.c, r.seed, expected_edges=len(r.stream),
-                                    max_batch=min(r.chunk, max(1, len(r.stream))), stream=copy_stream)
+                                    max_batch=feed(r), stream=copy_stream)
             hsrc, hdst = host_edges(r)
             with torch.cuda.stream(copy_stream):
                 src = hsrc.to("cuda", non_blocking=True)
@@ -206,7 +210,7 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
             if not x.waited:
                 compute.wait_event(x.ready)
                 x.waited = True
-            n = min(x.req.chunk, len(x.req.stream) - x.fed)
+            n = min(feed(x.req), len(x.req.stream) - x.fed)
             hs.append(x.handle)
             a.append(x.src[x.fed:x.fed + n])
             b.append(x.dst[x.fed:x.fed + n])
