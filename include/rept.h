@@ -8,7 +8,7 @@
  * v among the edges it already keeps (Algorithm 1, UpdateTriangleCNT).  The
  * counts tau^(i), tau_v^(i) are combined into estimates of the global and
  * local triangle counts (Section III-A for c <= m, Section III-B.1 for c > m
- * with c mod m = 0).
+ * with c mod m = 0, Section III-B.2 / Algorithm 2 for c > m with c mod m != 0).
  *
  * Conventions shared by every entry point
  *   - Processors are 0-based: processor i = k*m + j (i < c) is slot j of hash
@@ -49,7 +49,7 @@ extern "C" {
 #endif
 
 #define REPT_OK 0
-#define REPT_E_INVAL (-1)     /* bad argument (m, c or n_nodes zero, NULL pointer, unsupported c) */
+#define REPT_E_INVAL (-1)     /* bad argument (m, c or n_nodes zero, NULL pointer, unsupported combination) */
 #define REPT_E_RANGE (-2)     /* an edge endpoint >= n_nodes (device-detected, batch not applied) */
 #define REPT_E_CAPACITY (-3)  /* REPT_FLAG_FIXED_POOL set and the adjacency pool is full (batch not applied) */
 #define REPT_E_NOMEM (-4)     /* a device or pinned-host allocation failed */
@@ -75,7 +75,7 @@ extern "C" {
 
 typedef struct rept_config {
     uint32_t m;              /* 1/p; m >= 1 (the paper takes m >= 2; m = 1 keeps every edge) */
-    uint32_t c;              /* number of processors, c >= 1; c > m requires c % m == 0 */
+    uint32_t c;              /* number of processors, 1 <= c <= 4096 */
     uint64_t seed;           /* hash seed s_0 */
     uint32_t n_nodes;        /* node ids are < n_nodes; 1 <= n_nodes < 2^32 - 1 */
     uint32_t flags;          /* REPT_FLAG_* */
@@ -113,8 +113,10 @@ typedef struct rept_state rept_state;
  * rept_create: allocate an empty stream state (all tau^(i), tau_v^(i) = 0,
  * every E^(i) empty; Algorithm 1's initialisation) on the current device.
  * `cfg` is copied; `*out` receives the handle (owned by the caller, released
- * with rept_destroy).  Returns REPT_E_INVAL for m == 0, c == 0, n_nodes == 0
- * or c > m with c % m != 0; REPT_E_NOMEM / REPT_E_CUDA on allocation failure.
+ * with rept_destroy).  Returns REPT_E_INVAL for m == 0, c == 0, c > 4096 or
+ * n_nodes == 0; REPT_E_NOMEM / REPT_E_CUDA on allocation failure.  For c > m
+ * with c mod m != 0 the handle also keeps Algorithm 2's triangle-pair
+ * counters (16 + 12 * ceil(c/m) bytes per stream edge).
  */
 int rept_create(const rept_config* cfg, void* stream, rept_state** out);
 
@@ -158,6 +160,11 @@ int rept_ingest_host(rept_state* s, const uint32_t* h_src, const uint32_t* h_dst
  * rept_estimates: FP64 estimates from the counts so far.
  *   c <= m              : tau_hat = (m^2 / c) * sum_i tau^(i),  tau_hat_v likewise   (Section III-A)
  *   c > m, c % m == 0   : tau_hat = (m / c1) * sum_i tau^(i), c1 = c / m              (Section III-B.1)
+ *   c > m, c % m != 0   : the full groups' estimate t1 = (m / c1) * sum_{i < c1 m} tau^(i) and the
+ *                         partial group's t2 = (m^2 / c2) * sum_{i >= c1 m} tau^(i), combined as
+ *                         (w2 t1 + w1 t2) / (w1 + w2) with w1 = t1 (m-1) / c1 and
+ *                         w2 = (t1 (m^2 - c2) + 2 eta_hat (m - c2)) / c2, eta_hat = (m^3/c) sum_i eta^(i)
+ *                         (Algorithm 2; t1 when both weights are 0); locally the same per node
  * Each scale factor is formed in double and multiplied by the exactly
  * converted integer sum.  h_global: host double (required).  d_local: device
  * array of n_nodes doubles, or NULL to skip the local estimates.
@@ -187,6 +194,18 @@ int rept_estimates_async(rept_state* s, double* h_global, uint64_t* h_proc, uint
  * Synchronises `stream`; returns any sticky device error.
  */
 int rept_counts(rept_state* s, uint64_t* h_proc, uint64_t* d_local, void* stream);
+
+/*
+ * rept_pair_counts: for c > m with c mod m != 0, Algorithm 2's counters:
+ * h_eta_proc (host, c uint64: eta^(i)), d_eta_local (device, n_nodes uint64:
+ * sum_i eta_v^(i)), d_local1 / d_local2 (device, n_nodes uint64: sum of
+ * tau_v^(i) over the full groups / over the partial group); any may be NULL.
+ * The pair counter of a newly stored edge starts at 0 (Table I's eta counts
+ * only pairs whose shared edge is last in neither triangle).  REPT_E_INVAL
+ * for other c.  Synchronises `stream`; returns any sticky device error.
+ */
+int rept_pair_counts(rept_state* s, uint64_t* h_eta_proc, uint64_t* d_eta_local, uint64_t* d_local1,
+                     uint64_t* d_local2, void* stream);
 
 /* rept_stats: counters describing the handle (see rept_stats).  Synchronises `stream`. */
 int rept_get_stats(rept_state* s, rept_stats* out, void* stream);

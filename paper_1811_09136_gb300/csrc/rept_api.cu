@@ -193,7 +193,42 @@ int fold_times(rept_state* s) {
     return REPT_OK;
 }
 
+// Pair arrays (Algorithm 2) covering stream indices < edges; grows by copying (synchronises).
+int ensure_pair_capacity(rept_state* s, unsigned long long edges, cudaStream_t st) {
+    StreamDev& d = s->d;
+    if (edges <= d.pair_cap) return REPT_OK;
+    const unsigned long long cap = std::max(edges, 2 * d.pair_cap), G = s->groups, old = d.pair_cap;
+    uint2* ends = nullptr;
+    uint32_t *tau = nullptr, *evt = nullptr, *lst = nullptr;
+    int rc = dev_alloc(s, (void**)&ends, cap * sizeof(uint2));
+    if (!rc) rc = dev_alloc(s, (void**)&tau, cap * G * sizeof(uint32_t));
+    if (!rc) rc = dev_alloc(s, (void**)&evt, cap * G * sizeof(uint32_t));
+    if (!rc) rc = dev_alloc(s, (void**)&lst, cap * G * sizeof(uint32_t));
+    if (rc) return rc;
+    REPT_CUDA(cudaMemsetAsync(tau, 0, cap * G * sizeof(uint32_t), st));
+    REPT_CUDA(cudaMemsetAsync(evt, 0, cap * G * sizeof(uint32_t), st));
+    if (old) {
+        REPT_CUDA(cudaMemcpyAsync(ends, d.edge_ends, old * sizeof(uint2), cudaMemcpyDeviceToDevice, st));
+        REPT_CUDA(cudaMemcpyAsync(tau, d.pair_tau, old * G * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    }
+    REPT_CUDA(cudaStreamSynchronize(st));
+    dev_free(s, d.edge_ends, old * sizeof(uint2));
+    dev_free(s, d.pair_tau, old * G * sizeof(uint32_t));
+    dev_free(s, d.pair_evt, old * G * sizeof(uint32_t));
+    dev_free(s, d.pair_list, old * G * sizeof(uint32_t));
+    d.edge_ends = ends;
+    d.pair_tau = tau;
+    d.pair_evt = evt;
+    d.pair_list = lst;
+    d.pair_cap = cap;
+    return REPT_OK;
+}
+
 int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, unsigned long long n, cudaStream_t st) {
+    if (s->d.pair_tau) {
+        const int prc = ensure_pair_capacity(s, s->next_t + n, st);
+        if (prc) return prc;
+    }
     BatchDev b{d_src, d_dst, n, s->next_t};
     const int threads = 256;
     const unsigned long long want_blocks = (n + threads - 1) / threads;
@@ -231,14 +266,11 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
     else
         rc = timed_launch(s, REPT_K_INTERSECT, st, [&] { k_intersect<false><<<grid_i, 256, smem, st>>>(s->d, b); });
     if (rc) return rc;
+    if (s->d.pair_tau &&
+        (rc = timed_launch(s, REPT_K_INTERSECT, st, [&] { k_pairs<<<s->sm_count * 4, 256, 0, st>>>(s->d); })))
+        return rc;
     s->next_t += n;
     return REPT_OK;
-}
-
-int sync_status(rept_state* s, cudaStream_t st) {
-    int rc = read_ctrl(s, st);
-    if (rc) return rc;
-    return status_to_code(s->h_ctrl->status);
 }
 
 // f such that tau_hat = f * (integer sum): m^2 / c for c <= m, m / c1 for c = c1 * m.
@@ -248,6 +280,24 @@ double estimate_factor(const rept_config& c) {
     return md / (double)(c.c / c.m);
 }
 
+// tau_hat into s->d_global: Section III-A / III-B.1 factor, or Algorithm 2's combination.
+int enqueue_global_estimate(rept_state* s, cudaStream_t st) {
+    if (s->d.local2)
+        return timed_launch(s, REPT_K_ESTIMATE, st, [&] {
+            k_global_estimate_partial<<<1, 32, 0, st>>>(s->d.proc, s->d.eta_proc, s->cfg.m, s->cfg.c, s->d_global);
+        });
+    const double f = estimate_factor(s->cfg);
+    return timed_launch(s, REPT_K_ESTIMATE, st,
+                        [&] { k_global_estimate<<<1, 256, 0, st>>>(s->d.proc, s->cfg.c, f, s->d_global); });
+}
+
+int sync_status(rept_state* s, cudaStream_t st) {
+    int rc = read_ctrl(s, st);
+    if (rc) return rc;
+    return status_to_code(s->h_ctrl->status);
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -256,7 +306,6 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if (!cfg || !out) return REPT_E_INVAL;
     *out = nullptr;
     if (cfg->m == 0 || cfg->c == 0 || cfg->n_nodes == 0 || cfg->n_nodes == 0xFFFFFFFFu) return REPT_E_INVAL;
-    if (cfg->c > cfg->m && cfg->c % cfg->m != 0) return REPT_E_INVAL;
     if (cfg->c > kMaxProcessors) return REPT_E_INVAL;
     if (cfg->tile_max != 0 && cfg->tile_max != 4 && cfg->tile_max != 8 && cfg->tile_max != 16 &&
         cfg->tile_max != 32)
@@ -280,7 +329,7 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
         return fail(REPT_E_CUDA);
     s->grid_intersect = s->sm_count * std::max(per_sm, 1);
     s->grid_stream = s->sm_count * 8;
-    s->groups = cfg->c <= cfg->m ? 1u : cfg->c / cfg->m;
+    s->groups = cfg->c <= cfg->m ? 1u : (cfg->c + cfg->m - 1) / cfg->m;
     const uint32_t n = cfg->n_nodes;
     StreamDev& d = s->d;
     d.m = cfg->m;
@@ -302,6 +351,14 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if ((rc = dev_alloc(s, (void**)&d.pool, quads * 32ull))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&s->d_global, sizeof(double)))) return fail(rc);
     d.pool_quads = quads;
+    d.c1 = cfg->c <= cfg->m ? cfg->c : cfg->c / cfg->m;
+    if (cfg->c > cfg->m && cfg->c % cfg->m != 0) {
+        // Algorithm 2: the partial group's local counts and the triangle-pair counters
+        if ((rc = dev_alloc(s, (void**)&d.local2, (size_t)n * sizeof(unsigned long long)))) return fail(rc);
+        if ((rc = dev_alloc(s, (void**)&d.eta_proc, (size_t)cfg->c * sizeof(unsigned long long)))) return fail(rc);
+        if ((rc = dev_alloc(s, (void**)&d.eta_local, (size_t)n * sizeof(unsigned long long)))) return fail(rc);
+        if ((rc = ensure_pair_capacity(s, std::max<unsigned long long>(cfg->expected_edges, mb), st))) return fail(rc);
+    }
     if ((rc = ensure_batch_scratch(s, mb, st))) return fail(rc);
     if (cudaMallocHost((void**)&s->h_ctrl, sizeof(Ctrl)) != cudaSuccess) return fail(REPT_E_NOMEM);
     if (cudaMallocHost((void**)&s->h_global, sizeof(double)) != cudaSuccess) return fail(REPT_E_NOMEM);
@@ -330,6 +387,13 @@ int rept_reset(rept_state* s, void* stream) {
     REPT_CUDA(cudaMemsetAsync(d.local, 0, n * sizeof(unsigned long long), st));
     REPT_CUDA(cudaMemsetAsync(d.proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
     REPT_CUDA(cudaMemsetAsync(d.add, 0, n * sizeof(uint32_t), st));
+    if (d.local2) REPT_CUDA(cudaMemsetAsync(d.local2, 0, n * sizeof(unsigned long long), st));
+    if (d.eta_local) REPT_CUDA(cudaMemsetAsync(d.eta_local, 0, n * sizeof(unsigned long long), st));
+    if (d.eta_proc) REPT_CUDA(cudaMemsetAsync(d.eta_proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
+    if (d.pair_tau) {
+        REPT_CUDA(cudaMemsetAsync(d.pair_tau, 0, d.pair_cap * s->groups * sizeof(uint32_t), st));
+        REPT_CUDA(cudaMemsetAsync(d.pair_evt, 0, d.pair_cap * s->groups * sizeof(uint32_t), st));
+    }
     REPT_CUDA(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), st));
     REPT_CUDA(cudaStreamSynchronize(st));
     memset(s->h_ctrl, 0, sizeof(Ctrl));
@@ -349,6 +413,13 @@ int rept_reset_async(rept_state* s, uint64_t seed, void* stream) {
     REPT_CUDA(cudaMemsetAsync(d.local, 0, n * sizeof(unsigned long long), st));
     REPT_CUDA(cudaMemsetAsync(d.proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
     REPT_CUDA(cudaMemsetAsync(d.add, 0, n * sizeof(uint32_t), st));
+    if (d.local2) REPT_CUDA(cudaMemsetAsync(d.local2, 0, n * sizeof(unsigned long long), st));
+    if (d.eta_local) REPT_CUDA(cudaMemsetAsync(d.eta_local, 0, n * sizeof(unsigned long long), st));
+    if (d.eta_proc) REPT_CUDA(cudaMemsetAsync(d.eta_proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
+    if (d.pair_tau) {
+        REPT_CUDA(cudaMemsetAsync(d.pair_tau, 0, d.pair_cap * s->groups * sizeof(uint32_t), st));
+        REPT_CUDA(cudaMemsetAsync(d.pair_evt, 0, d.pair_cap * s->groups * sizeof(uint32_t), st));
+    }
     REPT_CUDA(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), st));
     s->next_t = 0;
     return REPT_OK;
@@ -403,14 +474,20 @@ int rept_ingest_host(rept_state* s, const uint32_t* h_src, const uint32_t* h_dst
 int rept_estimates(rept_state* s, double* h_global, double* d_local, void* stream) {
     if (!s || !h_global) return REPT_E_INVAL;
     cudaStream_t st = as_stream(stream);
-    const double f = estimate_factor(s->cfg);
-    int rc0 = timed_launch(s, REPT_K_ESTIMATE, st,
-                           [&] { k_global_estimate<<<1, 256, 0, st>>>(s->d.proc, s->cfg.c, f, s->d_global); });
+    int rc0 = enqueue_global_estimate(s, st);
     if (rc0) return rc0;
     if (d_local) {
-        rc0 = timed_launch(s, REPT_K_ESTIMATE, st, [&] {
-            k_local_estimates<<<s->sm_count * 4, 256, 0, st>>>(s->d.local, s->d.n_nodes, f, d_local);
-        });
+        if (s->d.local2) {
+            rc0 = timed_launch(s, REPT_K_ESTIMATE, st, [&] {
+                k_local_estimates_partial<<<s->sm_count * 4, 256, 0, st>>>(s->d.local, s->d.local2, s->d.eta_local,
+                                                                           s->d.n_nodes, s->cfg.m, s->cfg.c, d_local);
+            });
+        } else {
+            const double f = estimate_factor(s->cfg);
+            rc0 = timed_launch(s, REPT_K_ESTIMATE, st, [&] {
+                k_local_estimates<<<s->sm_count * 4, 256, 0, st>>>(s->d.local, s->d.n_nodes, f, d_local);
+            });
+        }
         if (rc0) return rc0;
     }
     REPT_CUDA(cudaMemcpyAsync(s->h_global, s->d_global, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -422,9 +499,7 @@ int rept_estimates(rept_state* s, double* h_global, double* d_local, void* strea
 int rept_estimates_async(rept_state* s, double* h_global, uint64_t* h_proc, uint32_t* h_status, void* stream) {
     if (!s || !h_global || !h_status) return REPT_E_INVAL;
     cudaStream_t st = as_stream(stream);
-    const double f = estimate_factor(s->cfg);
-    int rc = timed_launch(s, REPT_K_ESTIMATE, st,
-                          [&] { k_global_estimate<<<1, 256, 0, st>>>(s->d.proc, s->cfg.c, f, s->d_global); });
+    int rc = enqueue_global_estimate(s, st);
     if (rc) return rc;
     REPT_CUDA(cudaMemcpyAsync(h_global, s->d_global, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (h_proc)
@@ -459,9 +534,32 @@ int rept_counts(rept_state* s, uint64_t* h_proc, uint64_t* d_local, void* stream
     if (h_proc)
         REPT_CUDA(cudaMemcpyAsync(h_proc, s->d.proc, (size_t)s->cfg.c * sizeof(uint64_t), cudaMemcpyDeviceToHost,
                                   st));
-    if (d_local)
-        REPT_CUDA(cudaMemcpyAsync(d_local, s->d.local, (size_t)s->d.n_nodes * sizeof(uint64_t),
-                                  cudaMemcpyDeviceToDevice, st));
+    if (d_local) {
+        if (s->d.local2) {
+            k_add_local<<<s->sm_count * 4, 256, 0, st>>>(s->d.local, s->d.local2, s->d.n_nodes,
+                                                        reinterpret_cast<unsigned long long*>(d_local));
+            g_launches.fetch_add(1, std::memory_order_relaxed);
+        } else {
+            REPT_CUDA(cudaMemcpyAsync(d_local, s->d.local, (size_t)s->d.n_nodes * sizeof(uint64_t),
+                                      cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    return sync_status(s, st);
+}
+
+int rept_pair_counts(rept_state* s, uint64_t* h_eta_proc, uint64_t* d_eta_local, uint64_t* d_local1,
+                     uint64_t* d_local2, void* stream) {
+    if (!s) return REPT_E_INVAL;
+    if (!s->d.local2) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    const size_t n = s->d.n_nodes;
+    if (h_eta_proc)
+        REPT_CUDA(cudaMemcpyAsync(h_eta_proc, s->d.eta_proc, (size_t)s->cfg.c * sizeof(uint64_t),
+                                  cudaMemcpyDeviceToHost, st));
+    if (d_eta_local)
+        REPT_CUDA(cudaMemcpyAsync(d_eta_local, s->d.eta_local, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+    if (d_local1) REPT_CUDA(cudaMemcpyAsync(d_local1, s->d.local, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+    if (d_local2) REPT_CUDA(cudaMemcpyAsync(d_local2, s->d.local2, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
     return sync_status(s, st);
 }
 
@@ -523,6 +621,13 @@ void rept_destroy(rept_state* s) {
     cudaFree(d.big);
     cudaFree(d.rec);
     cudaFree(d.srec);
+    cudaFree(d.local2);
+    cudaFree(d.eta_proc);
+    cudaFree(d.eta_local);
+    cudaFree(d.edge_ends);
+    cudaFree(d.pair_tau);
+    cudaFree(d.pair_evt);
+    cudaFree(d.pair_list);
     cudaFree(d.hist);
     cudaFree(s->stage_src);
     cudaFree(s->stage_dst);
@@ -686,7 +791,7 @@ int rept_group_ingest(rept_group* g, rept_state* const* hs, const uint32_t* cons
     bool guaranteed = true;
     for (uint32_t i = 0; i < k; ++i) {
         rept_state* s = hs[i];
-        if (!s) return REPT_E_INVAL;
+        if (!s || s->d.local2) return REPT_E_INVAL;  // c mod m != 0 is served by the single-stream path
         if (n[i] && (!d_src[i] || !d_dst[i])) return REPT_E_INVAL;
         if (s->next_t + n[i] >= 0xFFFFFFFEull) return REPT_E_INVAL;
         int rc = ensure_batch_scratch(s, std::max<unsigned long long>(n[i], 1ull), st);

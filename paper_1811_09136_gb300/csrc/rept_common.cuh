@@ -99,6 +99,7 @@ struct Ctrl {
     unsigned long long bin_start[kBins];
     unsigned long long bin_count[kBins];
     unsigned long long bin_next[kBins];
+    unsigned long long n_pairs;  // entries of pair_list this batch
     unsigned long long n_big;   // nodes whose table (32..2048 slots) k_rehash_big moves, a warp each
     unsigned long long n_huge;  // nodes whose table (>= 4096 slots) k_rehash_huge moves, a block each
     unsigned long long huge_next;
@@ -136,6 +137,17 @@ struct StreamDev {
                         // k_rehash_big list from the front, the k_rehash_huge list from the back
     unsigned long long big_cap;
     Ctrl* ctrl;
+    // c > m with c mod m != 0 (Algorithm 2): the partial group's local counts and the triangle-pair
+    // counters; all NULL otherwise
+    uint32_t c1;                    // full groups: processors i < c1 * m feed `local`, the rest `local2`
+    unsigned long long* local2;     // [n_nodes] sum of tau_v^(i) over the partial group
+    unsigned long long* eta_proc;   // [c] eta^(i)
+    unsigned long long* eta_local;  // [n_nodes] sum over processors of eta_v^(i)
+    uint2* edge_ends;               // [pair_cap] endpoints of the stored edge with stream index t
+    uint32_t* pair_tau;             // [pair_cap * groups] tau_(e)^(i) of edge e in group k (Algorithm 2)
+    uint32_t* pair_evt;             // [pair_cap * groups] this batch's closed wedges through (e, k)
+    uint32_t* pair_list;            // [pair_cap * groups] the (e, k) with events this batch: e * groups + k
+    unsigned long long pair_cap;    // stream indices covered by the pair arrays
 };
 
 // One batch of edges appended to a stream.

@@ -46,6 +46,7 @@ __device__ __forceinline__ void k_classify_body(const StreamDev& d, const BatchD
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < kSortBuckets; i += gridDim.x * blockDim.x)
         d.hist[i] = 0u;
     if (blockIdx.x == 0 && threadIdx.x < kBins) d.ctrl->bin_next[threadIdx.x] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->n_pairs = 0ull;
     if (d.ctrl->status) return;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -233,6 +234,7 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
                 const uint32_t pu = mu.y - atomicSub(&d.add[u], 1u), pv = mv.y - atomicSub(&d.add[v], 1u);
                 d.pool[4ull * mu.x + (1ull << lu) + pu] = make_uint2(v, t);
                 d.pool[4ull * mv.x + (1ull << lv) + pv] = make_uint2(u, t);
+                if (d.edge_ends) d.edge_ends[t] = make_uint2(u, v);
             }
             // an edge can close wedges only if both endpoints have stored edges
             if (mu.y != 0u && mv.y != 0u) {
@@ -363,15 +365,32 @@ struct Work {
 // Wedge (s, w), (l, w), both edges older than the arriving edge (s, l): count it for every hash group
 // whose colour of the two edges agrees and names a kept processor, and add the number of such groups
 // to tau_s, tau_l and tau_w (Algorithm 1's local updates, one wedge at a time).
+// Algorithm 2's pair counters: one more closed wedge through stored edge t in group k this batch.
+__device__ __forceinline__ void pair_event(const StreamDev& d, uint32_t t, uint32_t k) {
+    const unsigned long long idx = (unsigned long long)t * d.groups + k;
+    if (atomicAdd(&d.pair_evt[idx], 1u) == 0u) d.pair_list[atomicAdd(&d.ctrl->n_pairs, 1ull)] = (uint32_t)idx;
+}
+
 __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, uint32_t l, uint32_t w,
                                                 unsigned long long* s_proc) {
-    uint32_t found = 0;
+    uint32_t found = 0, found2 = 0;
+    uint32_t t_sw = kEmptyId, t_lw = kEmptyId;
     for (uint32_t k = 0; k < d.groups; ++k) {
         const uint64_t sk = group_seed(d.seed, k);
         const uint32_t js = colour_of(s, w, sk, d.fm);
         if (k * d.m + js < d.c && colour_of(l, w, sk, d.fm) == js) {
-            ++found;
             atomicAdd(&s_proc[k * d.m + js], 1ull);
+            if (d.local2 && k >= d.c1) ++found2; else ++found;
+            if (d.pair_tau) {
+                if (t_sw == kEmptyId) {  // the wedge's two stream indices, looked up once
+                    uint32_t ns;
+                    const uint2 ms = d.meta[s], ml = d.meta[l];
+                    t_sw = table_find(d.pool, 4ull * ms.x, table_lg(ms.y), w, ns);
+                    t_lw = table_find(d.pool, 4ull * ml.x, table_lg(ml.y), w, ns);
+                }
+                pair_event(d, t_sw, k);
+                pair_event(d, t_lw, k);
+            }
         }
     }
     if (found) {
@@ -379,7 +398,12 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
         atomicAdd(&d.local[s], (unsigned long long)found);
         atomicAdd(&d.local[l], (unsigned long long)found);
     }
-    return found;
+    if (found2) {
+        atomicAdd(&d.local2[w], (unsigned long long)found2);
+        atomicAdd(&d.local2[s], (unsigned long long)found2);
+        atomicAdd(&d.local2[l], (unsigned long long)found2);
+    }
+    return found + found2;
 }
 
 // Per-warp queue of closed wedges (s, l, w) in shared memory.  Wedges are pushed as the probes find
@@ -853,6 +877,74 @@ __global__ void __launch_bounds__(256, 5) k_intersect_group(const StreamDev* __r
     group_drain_tiles<8>(ds, k, 1, pref, cursor, q);
     group_drain_tiles<4>(ds, k, 0, pref, cursor, q);
     if (q.n) gq_flush(ds, q, q.n);
+}
+
+// Algorithm 2's triangle-pair counters, folded in after the intersection.  Edge e of group k was a
+// wedge edge of kcnt closed wedges this batch, all for the processor i = k*m + h_k(e).  In stream
+// order they saw the counter values B, B+1, ..., B+kcnt-1 (B its value before the batch), so their
+// contribution to eta^(i) and to eta_x, eta_y of e's endpoints is kcnt*B + kcnt*(kcnt-1)/2, whatever
+// their order; then the counter advances by kcnt.  (The counter of a newly stored edge starts at 0.)
+__global__ void k_pairs(StreamDev d) {
+    if (d.ctrl->status) return;
+    const unsigned long long n = d.ctrl->n_pairs;
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t idx = d.pair_list[q];
+        const uint32_t t = idx / d.groups, k = idx % d.groups;
+        const unsigned long long kc = d.pair_evt[idx], base = d.pair_tau[idx];
+        const unsigned long long add = kc * base + kc * (kc - 1) / 2;
+        const uint2 e = d.edge_ends[t];
+        const uint32_t i = k * d.m + colour_of(e.x, e.y, group_seed(d.seed, k), d.fm);
+        atomicAdd(&d.eta_proc[i], add);
+        atomicAdd(&d.eta_local[e.x], add);
+        atomicAdd(&d.eta_local[e.y], add);
+        d.pair_tau[idx] = (uint32_t)(base + kc);
+        d.pair_evt[idx] = 0u;
+    }
+}
+
+// Algorithm 2's estimates (c > m, c mod m != 0): the two group estimates combined with the plug-in
+// inverse-variance weights; with both weights zero the full groups' estimate.  Same expression order
+// as the scalar formulas of Section III-B.2.
+__device__ __forceinline__ double combine_estimates(double t1, double t2, double eta_hat, double md, double c1,
+                                                    double c2) {
+    const double w1 = t1 * (md - 1.0) / c1;
+    const double w2 = (t1 * (md * md - c2) + 2.0 * eta_hat * (md - c2)) / c2;
+    return (w1 + w2 > 0.0) ? (w2 * t1 + w1 * t2) / (w1 + w2) : t1;
+}
+
+__global__ void k_global_estimate_partial(const unsigned long long* __restrict__ proc,
+                                          const unsigned long long* __restrict__ eta, uint32_t m, uint32_t c,
+                                          double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint32_t c1 = c / m, c2 = c % m;
+    unsigned long long s1 = 0, s2 = 0, se = 0;
+    for (uint32_t i = 0; i < c1 * m; ++i) s1 += proc[i];
+    for (uint32_t i = c1 * m; i < c; ++i) s2 += proc[i];
+    for (uint32_t i = 0; i < c; ++i) se += eta[i];
+    const double md = (double)m;
+    const double t1 = (double)s1 * (md / (double)c1), t2 = (double)s2 * (md * md / (double)c2);
+    const double eta_hat = (double)se * (md * md * md / (double)c);
+    *out = combine_estimates(t1, t2, eta_hat, md, (double)c1, (double)c2);
+}
+
+__global__ void k_local_estimates_partial(const unsigned long long* __restrict__ l1,
+                                          const unsigned long long* __restrict__ l2,
+                                          const unsigned long long* __restrict__ el, uint32_t n, uint32_t m,
+                                          uint32_t c, double* __restrict__ out) {
+    const uint32_t c1 = c / m, c2 = c % m;
+    const double md = (double)m;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const double a1 = (double)l1[v] * (md / (double)c1), a2 = (double)l2[v] * (md * md / (double)c2);
+        const double eh = (double)el[v] * (md * md * md / (double)c);
+        out[v] = combine_estimates(a1, a2, eh, md, (double)c1, (double)c2);
+    }
+}
+
+// sum_i tau_v^(i) over all processors when the local counts are split in two.
+__global__ void k_add_local(const unsigned long long* __restrict__ a, const unsigned long long* __restrict__ b,
+                            uint32_t n, unsigned long long* __restrict__ out) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) out[v] = a[v] + b[v];
 }
 
 // Kernel entry points.  Each batch kernel exists twice: for one stream (state and batch passed by

@@ -77,6 +77,7 @@ def load():
             "rept_estimates_host": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
             "rept_estimates_async": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
             "rept_counts": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+            "rept_pair_counts": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
             "rept_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats), _vp]),
             "rept_sync": (ctypes.c_int, [_vp, _vp]),
             "rept_kernel_times": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
@@ -234,6 +235,17 @@ class ReptStream:
             return proc, local, rc
         _check(rc, "rept_counts")
         return proc, local
+
+    def pair_counts(self, stream=None):
+        """c > m with c mod m != 0 (Algorithm 2): (eta^(i) numpy uint64 [c], sum_i eta_v^(i),
+        full-group local counts, partial-group local counts), the last three int64 CUDA tensors."""
+        import torch
+        eta = np.zeros(self.c, dtype=np.uint64)
+        el, l1, l2 = (torch.empty(self.n_nodes, dtype=torch.int64, device="cuda") for _ in range(3))
+        _check(self._lib.rept_pair_counts(self._h, ctypes.c_void_p(eta.ctypes.data), ctypes.c_void_p(el.data_ptr()),
+                                          ctypes.c_void_p(l1.data_ptr()), ctypes.c_void_p(l2.data_ptr()),
+                                          _cur_stream(stream)), "rept_pair_counts")
+        return eta, el, l1, l2
 
     def stats(self, stream=None) -> dict:
         st = Stats()

@@ -40,5 +40,5 @@ def test_create_rejects_bad_config_before_touching_the_device():
     lib = ctypes.CDLL(_build.build())
     h = ctypes.c_void_p()
     for cfg in (Config(0, 1, 1, 10, 0, 0, 0), Config(4, 0, 1, 10, 0, 0, 0), Config(4, 4, 1, 0, 0, 0, 0),
-                Config(3, 7, 1, 10, 0, 0, 0), Config(4, 4, 1, 10, 0, 0, 0, 12, 0), Config(4, 4, 1, 10, 0, 0, 0, 0, 1)):
+                Config(3, 5000, 1, 10, 0, 0, 0), Config(4, 4, 1, 10, 0, 0, 0, 12, 0), Config(4, 4, 1, 10, 0, 0, 0, 0, 1)):
         assert lib.rept_create(ctypes.byref(cfg), None, ctypes.byref(h)) == -1

@@ -162,10 +162,29 @@ def test_large_node_ids():
     assert int(local[: n - 64].sum()) == 0
 
 
-def test_unsupported_partial_group_rejected():
-    from paper_1811_09136_gb300.rept import ReptStream, ReptError
-    with pytest.raises(ReptError):
-        ReptStream(100, 3, 7, 1)
+@pytest.mark.parametrize("m,c", [(3, 7), (4, 9), (2, 3), (5, 12), (3, 4)])
+def test_partial_group_algorithm2(m, c):
+    """c > m with c mod m != 0: tau^(i), the split local counts, the triangle-pair counters eta^(i)
+    and sum_i eta_v^(i), and the combined estimates all match the oracle, for every batch split."""
+    s = gg.chung_lu(3000, 2.2, 25_000, graph_seed=m, order_seed=c)
+    ref = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, 7)
+    ref_g, ref_loc = O.estimates(m, c, ref, s.n_nodes)
+    from paper_1811_09136_gb300.rept import ReptStream
+    src, dst = device_edges(s)
+    for batch in (len(s), 997, 1 << 13):
+        with ReptStream(s.n_nodes, m, c, 7, max_batch=batch) as r:
+            for off in range(0, len(s), batch):
+                r.ingest(src[off:off + batch], dst[off:off + batch])
+            proc, local = r.counts()
+            eta, el, l1, l2 = r.pair_counts()
+            g, loc = r.estimates()
+        u64 = lambda t: t.cpu().numpy().view(np.uint64)
+        assert np.array_equal(proc, ref.tau_proc), batch
+        assert np.array_equal(u64(l1), ref.local1) and np.array_equal(u64(l2), ref.local2), batch
+        assert np.array_equal(u64(local), ref.local1 + ref.local2), batch
+        assert np.array_equal(eta, ref.eta_proc), (batch, eta, ref.eta_proc)
+        assert np.array_equal(u64(el), ref.eta_local), batch
+        assert_estimates_close(g, loc.cpu().numpy(), ref_g, ref_loc)
 
 
 def test_work_counters_match_the_graph():
