@@ -62,6 +62,8 @@ extern "C" {
 #define REPT_FLAG_SYNC 2u       /* synchronise at the end of every ingest and report errors at once */
 #define REPT_FLAG_PROFILE 4u    /* time every kernel launch with CUDA events on its stream (rept_kernel_times) */
 #define REPT_FLAG_WORK_COUNTERS 8u /* count the intersection's table reads into rept_stats (slower; not for timing) */
+#define REPT_FLAG_LOCAL_PER_PROCESSOR 16u /* also keep every tau_v^(i) (c * n_nodes uint64), read with
+                                             rept_local_per_processor */
 
 /* kernel ids used by rept_kernel_times */
 #define REPT_K_CLASSIFY 0
@@ -207,6 +209,15 @@ int rept_counts(rept_state* s, uint64_t* h_proc, uint64_t* d_local, void* stream
 int rept_pair_counts(rept_state* s, uint64_t* h_eta_proc, uint64_t* d_eta_local, uint64_t* d_local1,
                      uint64_t* d_local2, void* stream);
 
+/*
+ * rept_local_per_processor: with REPT_FLAG_LOCAL_PER_PROCESSOR, every
+ * processor's local counts tau_v^(i) (Algorithm 1's per-processor counters)
+ * into the device array d_out of c * n_nodes uint64, processor-major
+ * (d_out[i * n_nodes + v]).  REPT_E_INVAL without the flag.  Synchronises
+ * `stream`; returns any sticky device error.
+ */
+int rept_local_per_processor(rept_state* s, uint64_t* d_out, void* stream);
+
 /* rept_stats: counters describing the handle (see rept_stats).  Synchronises `stream`. */
 int rept_get_stats(rept_state* s, rept_stats* out, void* stream);
 
@@ -218,6 +229,20 @@ int rept_get_stats(rept_state* s, rept_stats* out, void* stream);
  * the handle's recorded events.  REPT_E_INVAL without REPT_FLAG_PROFILE.
  */
 int rept_kernel_times(rept_state* s, double* ms, uint64_t* launches, int clear);
+
+/*
+ * Snapshot and resume.  rept_snapshot_size reports the bytes of the handle's
+ * current state (configuration, stream position, node tables, counters and,
+ * when kept, the pair counters and per-processor local counts); rept_snapshot
+ * copies it into caller-owned host memory h_buf of that many bytes.
+ * rept_restore loads such a snapshot into a handle created with the same
+ * m, c, seed, n_nodes and flags (REPT_E_INVAL otherwise), replacing its
+ * state; ingesting the rest of the stream then gives exactly the counts of
+ * an uninterrupted run.  All three synchronise `stream`.
+ */
+int rept_snapshot_size(rept_state* s, uint64_t* bytes, void* stream);
+int rept_snapshot(rept_state* s, void* h_buf, uint64_t bytes, void* stream);
+int rept_restore(rept_state* s, const void* h_buf, uint64_t bytes, void* stream);
 
 /* rept_sync: wait for `stream` and return the handle's sticky device error, if any. */
 int rept_sync(rept_state* s, void* stream);

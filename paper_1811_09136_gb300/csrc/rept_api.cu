@@ -352,6 +352,10 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if ((rc = dev_alloc(s, (void**)&s->d_global, sizeof(double)))) return fail(rc);
     d.pool_quads = quads;
     d.c1 = cfg->c <= cfg->m ? cfg->c : cfg->c / cfg->m;
+    if (cfg->flags & REPT_FLAG_LOCAL_PER_PROCESSOR) {
+        if ((rc = dev_alloc(s, (void**)&d.local_proc, (size_t)cfg->c * n * sizeof(unsigned long long))))
+            return fail(rc);
+    }
     if (cfg->c > cfg->m && cfg->c % cfg->m != 0) {
         // Algorithm 2: the partial group's local counts and the triangle-pair counters
         if ((rc = dev_alloc(s, (void**)&d.local2, (size_t)n * sizeof(unsigned long long)))) return fail(rc);
@@ -394,6 +398,7 @@ int rept_reset(rept_state* s, void* stream) {
         REPT_CUDA(cudaMemsetAsync(d.pair_tau, 0, d.pair_cap * s->groups * sizeof(uint32_t), st));
         REPT_CUDA(cudaMemsetAsync(d.pair_evt, 0, d.pair_cap * s->groups * sizeof(uint32_t), st));
     }
+    if (d.local_proc) REPT_CUDA(cudaMemsetAsync(d.local_proc, 0, (size_t)d.c * n * sizeof(unsigned long long), st));
     REPT_CUDA(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), st));
     REPT_CUDA(cudaStreamSynchronize(st));
     memset(s->h_ctrl, 0, sizeof(Ctrl));
@@ -420,6 +425,7 @@ int rept_reset_async(rept_state* s, uint64_t seed, void* stream) {
         REPT_CUDA(cudaMemsetAsync(d.pair_tau, 0, d.pair_cap * s->groups * sizeof(uint32_t), st));
         REPT_CUDA(cudaMemsetAsync(d.pair_evt, 0, d.pair_cap * s->groups * sizeof(uint32_t), st));
     }
+    if (d.local_proc) REPT_CUDA(cudaMemsetAsync(d.local_proc, 0, (size_t)d.c * n * sizeof(unsigned long long), st));
     REPT_CUDA(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), st));
     s->next_t = 0;
     return REPT_OK;
@@ -547,6 +553,122 @@ int rept_counts(rept_state* s, uint64_t* h_proc, uint64_t* d_local, void* stream
     return sync_status(s, st);
 }
 
+namespace {
+
+struct SnapHeader {
+    uint64_t magic, version;
+    uint64_t m, c, seed, n_nodes, flags, groups;
+    uint64_t next_t, pool_top, self_loops, stored;
+};
+constexpr uint64_t kSnapMagic = 0x5245505453544154ull;  // "REPTSTAT"
+
+// The arrays of a snapshot after the header, in order: {device pointer, bytes}.
+struct SnapPart {
+    void* ptr;
+    unsigned long long bytes;
+};
+
+int snap_parts(rept_state* s, unsigned long long pool_top, SnapPart* parts, int* np) {
+    StreamDev& d = s->d;
+    const unsigned long long n = d.n_nodes, c = d.c, G = s->groups, T = s->next_t;
+    int k = 0;
+    parts[k++] = {d.meta, n * sizeof(uint2)};
+    parts[k++] = {d.local, n * 8ull};
+    parts[k++] = {d.proc, c * 8ull};
+    parts[k++] = {d.pool, pool_top * 32ull};
+    if (d.local2) {
+        parts[k++] = {d.local2, n * 8ull};
+        parts[k++] = {d.eta_proc, c * 8ull};
+        parts[k++] = {d.eta_local, n * 8ull};
+        parts[k++] = {d.edge_ends, T * sizeof(uint2)};
+        parts[k++] = {d.pair_tau, T * G * 4ull};
+    }
+    if (d.local_proc) parts[k++] = {d.local_proc, c * n * 8ull};
+    *np = k;
+    return REPT_OK;
+}
+
+}  // namespace
+
+int rept_snapshot_size(rept_state* s, uint64_t* bytes, void* stream) {
+    if (!s || !bytes) return REPT_E_INVAL;
+    int rc = sync_status(s, as_stream(stream));
+    if (rc) return rc;
+    SnapPart parts[16];
+    int np = 0;
+    snap_parts(s, s->h_ctrl->pool_top, parts, &np);
+    unsigned long long total = sizeof(SnapHeader);
+    for (int i = 0; i < np; ++i) total += parts[i].bytes;
+    *bytes = total;
+    return REPT_OK;
+}
+
+int rept_snapshot(rept_state* s, void* h_buf, uint64_t bytes, void* stream) {
+    if (!s || !h_buf) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    int rc = sync_status(s, st);
+    if (rc) return rc;
+    SnapPart parts[16];
+    int np = 0;
+    snap_parts(s, s->h_ctrl->pool_top, parts, &np);
+    unsigned long long total = sizeof(SnapHeader);
+    for (int i = 0; i < np; ++i) total += parts[i].bytes;
+    if (bytes < total) return REPT_E_INVAL;
+    SnapHeader h{kSnapMagic, 1, s->cfg.m, s->cfg.c, s->cfg.seed, s->cfg.n_nodes, s->cfg.flags, s->groups,
+                 s->next_t, s->h_ctrl->pool_top, s->h_ctrl->self_loops, s->h_ctrl->stored};
+    std::memcpy(h_buf, &h, sizeof(h));
+    char* out = static_cast<char*>(h_buf) + sizeof(h);
+    for (int i = 0; i < np; ++i) {
+        if (parts[i].bytes) REPT_CUDA(cudaMemcpyAsync(out, parts[i].ptr, parts[i].bytes, cudaMemcpyDeviceToHost, st));
+        out += parts[i].bytes;
+    }
+    REPT_CUDA(cudaStreamSynchronize(st));
+    return REPT_OK;
+}
+
+int rept_restore(rept_state* s, const void* h_buf, uint64_t bytes, void* stream) {
+    if (!s || !h_buf || bytes < sizeof(SnapHeader)) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    SnapHeader h;
+    std::memcpy(&h, h_buf, sizeof(h));
+    if (h.magic != kSnapMagic || h.version != 1 || h.m != s->cfg.m || h.c != s->cfg.c || h.seed != s->cfg.seed ||
+        h.n_nodes != s->cfg.n_nodes || h.flags != s->cfg.flags || h.groups != s->groups)
+        return REPT_E_INVAL;
+    int rc = rept_reset(s, stream);
+    if (rc) return rc;
+    if (h.pool_top > s->d.pool_quads && (rc = grow_pool(s, h.pool_top, st))) return rc;
+    s->next_t = h.next_t;
+    if (s->d.local2 && (rc = ensure_pair_capacity(s, std::max<unsigned long long>(h.next_t, 1), st))) return rc;
+    SnapPart parts[16];
+    int np = 0;
+    snap_parts(s, h.pool_top, parts, &np);
+    unsigned long long total = sizeof(SnapHeader);
+    for (int i = 0; i < np; ++i) total += parts[i].bytes;
+    if (bytes < total) return REPT_E_INVAL;
+    const char* in = static_cast<const char*>(h_buf) + sizeof(h);
+    for (int i = 0; i < np; ++i) {
+        if (parts[i].bytes) REPT_CUDA(cudaMemcpyAsync(parts[i].ptr, in, parts[i].bytes, cudaMemcpyHostToDevice, st));
+        in += parts[i].bytes;
+    }
+    // control block: the pool in use and the tallies; every per-batch counter starts at zero
+    Ctrl c{};
+    c.pool_top = h.pool_top;
+    c.self_loops = h.self_loops;
+    c.stored = h.stored;
+    std::memcpy(s->h_ctrl, &c, sizeof(Ctrl));
+    REPT_CUDA(cudaMemcpyAsync(s->d.ctrl, s->h_ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    REPT_CUDA(cudaStreamSynchronize(st));
+    return REPT_OK;
+}
+
+int rept_local_per_processor(rept_state* s, uint64_t* d_out, void* stream) {
+    if (!s || !d_out || !s->d.local_proc) return REPT_E_INVAL;
+    cudaStream_t st = as_stream(stream);
+    REPT_CUDA(cudaMemcpyAsync(d_out, s->d.local_proc, (size_t)s->cfg.c * s->d.n_nodes * sizeof(uint64_t),
+                              cudaMemcpyDeviceToDevice, st));
+    return sync_status(s, st);
+}
+
 int rept_pair_counts(rept_state* s, uint64_t* h_eta_proc, uint64_t* d_eta_local, uint64_t* d_local1,
                      uint64_t* d_local2, void* stream) {
     if (!s) return REPT_E_INVAL;
@@ -628,6 +750,7 @@ void rept_destroy(rept_state* s) {
     cudaFree(d.pair_tau);
     cudaFree(d.pair_evt);
     cudaFree(d.pair_list);
+    cudaFree(d.local_proc);
     cudaFree(d.hist);
     cudaFree(s->stage_src);
     cudaFree(s->stage_dst);

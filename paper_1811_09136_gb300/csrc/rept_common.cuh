@@ -148,6 +148,7 @@ struct StreamDev {
     uint32_t* pair_evt;             // [pair_cap * groups] this batch's closed wedges through (e, k)
     uint32_t* pair_list;            // [pair_cap * groups] the (e, k) with events this batch: e * groups + k
     unsigned long long pair_cap;    // stream indices covered by the pair arrays
+    unsigned long long* local_proc; // [c * n_nodes] tau_v^(i), processor-major (REPT_FLAG_LOCAL_PER_PROCESSOR)
 };
 
 // One batch of edges appended to a stream.

@@ -381,6 +381,12 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
         if (k * d.m + js < d.c && colour_of(l, w, sk, d.fm) == js) {
             atomicAdd(&s_proc[k * d.m + js], 1ull);
             if (d.local2 && k >= d.c1) ++found2; else ++found;
+            if (d.local_proc) {
+                unsigned long long* lp = d.local_proc + (unsigned long long)(k * d.m + js) * d.n_nodes;
+                atomicAdd(&lp[s], 1ull);
+                atomicAdd(&lp[l], 1ull);
+                atomicAdd(&lp[w], 1ull);
+            }
             if (d.pair_tau) {
                 if (t_sw == kEmptyId) {  // the wedge's two stream indices, looked up once
                     uint32_t ns;

@@ -22,6 +22,7 @@ FLAG_FIXED_POOL = 1
 FLAG_SYNC = 2
 FLAG_PROFILE = 4
 FLAG_WORK_COUNTERS = 8
+FLAG_LOCAL_PER_PROCESSOR = 16
 KERNELS = ("classify", "plan", "commit", "insert", "intersect", "estimate", "sort")
 
 
@@ -78,6 +79,10 @@ def load():
             "rept_estimates_async": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
             "rept_counts": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
             "rept_pair_counts": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+            "rept_local_per_processor": (ctypes.c_int, [_vp, _vp, _vp]),
+            "rept_snapshot_size": (ctypes.c_int, [_vp, _vp, _vp]),
+            "rept_snapshot": (ctypes.c_int, [_vp, _vp, _u64, _vp]),
+            "rept_restore": (ctypes.c_int, [_vp, _vp, _u64, _vp]),
             "rept_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(Stats), _vp]),
             "rept_sync": (ctypes.c_int, [_vp, _vp]),
             "rept_kernel_times": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
@@ -235,6 +240,29 @@ class ReptStream:
             return proc, local, rc
         _check(rc, "rept_counts")
         return proc, local
+
+    def local_per_processor(self, stream=None):
+        """tau_v^(i) of every processor as an int64 CUDA tensor [c, n_nodes] (needs FLAG_LOCAL_PER_PROCESSOR)."""
+        import torch
+        out = torch.empty((self.c, self.n_nodes), dtype=torch.int64, device="cuda")
+        _check(self._lib.rept_local_per_processor(self._h, ctypes.c_void_p(out.data_ptr()), _cur_stream(stream)),
+               "rept_local_per_processor")
+        return out
+
+    def snapshot(self, stream=None) -> np.ndarray:
+        """The whole stream state as a host byte array (see rept_snapshot)."""
+        n = ctypes.c_uint64()
+        _check(self._lib.rept_snapshot_size(self._h, ctypes.byref(n), _cur_stream(stream)), "rept_snapshot_size")
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(self._lib.rept_snapshot(self._h, ctypes.c_void_p(buf.ctypes.data), n.value, _cur_stream(stream)),
+               "rept_snapshot")
+        return buf
+
+    def restore(self, buf: np.ndarray, stream=None):
+        """Replace the state with a snapshot taken from a handle of the same configuration."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(self._lib.rept_restore(self._h, ctypes.c_void_p(buf.ctypes.data), buf.size, _cur_stream(stream)),
+               "rept_restore")
 
     def pair_counts(self, stream=None):
         """c > m with c mod m != 0 (Algorithm 2): (eta^(i) numpy uint64 [c], sum_i eta_v^(i),

@@ -202,3 +202,56 @@ def test_work_counters_match_the_graph():
     assert st["wedges"] == exact.triangles == st["counted"]
     assert st["probes"] <= st["small_entries"] <= st["small_slots"]
     assert 4 * st["probes"] <= st["probe_slots"] < 6 * st["probes"]
+
+
+@pytest.mark.parametrize("m,c", [(4, 4), (5, 3), (3, 6), (3, 7)])
+def test_local_per_processor(m, c):
+    """Every processor's tau_v^(i) equals the oracle's, and sums to 3 tau^(i) per processor."""
+    from paper_1811_09136_gb300.rept import ReptStream, FLAG_LOCAL_PER_PROCESSOR
+    s = gg.chung_lu(1500, 2.2, 12_000, graph_seed=c, order_seed=m)
+    ref = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, 3, per_proc_local=True)
+    src, dst = device_edges(s)
+    with ReptStream(s.n_nodes, m, c, 3, max_batch=2048, flags=FLAG_LOCAL_PER_PROCESSOR) as r:
+        for off in range(0, len(s), 2048):
+            r.ingest(src[off:off + 2048], dst[off:off + 2048])
+        lp = r.local_per_processor().cpu().numpy().view(np.uint64)
+        proc, _ = r.counts()
+    assert np.array_equal(lp, ref.tau_local_proc)
+    assert np.array_equal(lp.sum(axis=1), 3 * proc)
+
+
+@pytest.mark.parametrize("m,c,flags", [(10, 10, 0), (3, 7, 0), (4, 4, 16)])
+def test_snapshot_restore_resumes_exactly(m, c, flags):
+    """Half the stream, a snapshot to host memory, a fresh handle restored from it, the other half:
+    the same counts (and pair counters / per-processor locals when kept) as one uninterrupted run."""
+    from paper_1811_09136_gb300.rept import ReptStream, ReptError
+    s = gg.chung_lu(4000, 2.2, 30_000, graph_seed=m + c, order_seed=5)
+    src, dst = device_edges(s)
+    half = 13_337
+    with ReptStream(s.n_nodes, m, c, 9, max_batch=4096, flags=flags) as a:
+        for off in range(0, half, 4096):
+            e = min(half, off + 4096)
+            a.ingest(src[off:e], dst[off:e])
+        snap = a.snapshot()
+    with ReptStream(s.n_nodes, m, c, 9, max_batch=4096, flags=flags) as b:
+        b.restore(snap)
+        for off in range(half, len(s), 4096):
+            b.ingest(src[off:off + 4096], dst[off:off + 4096])
+        proc, local = b.counts()
+        g, _ = b.estimates(local=False)
+        extra = b.pair_counts()[0] if c > m and c % m else None
+        lp = b.local_per_processor().cpu().numpy() if flags else None
+        st = b.stats()
+    ref = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, 9, per_proc_local=bool(flags))
+    ref_g, _ = O.estimates(m, c, ref, s.n_nodes)
+    assert np.array_equal(proc, ref.tau_proc)
+    assert np.array_equal(local.cpu().numpy().view(np.uint64), ref.local1 + ref.local2)
+    assert abs(g - ref_g) <= 1e-12 * abs(ref_g)
+    assert st["edges"] == len(s)
+    if extra is not None:
+        assert np.array_equal(extra, ref.eta_proc)
+    if lp is not None:
+        assert np.array_equal(lp.view(np.uint64), ref.tau_local_proc)
+    with ReptStream(s.n_nodes, m, c, 10, max_batch=4096, flags=flags) as wrong_seed:
+        with pytest.raises(ReptError):
+            wrong_seed.restore(snap)
