@@ -63,6 +63,15 @@ def load_library(path: str):
     lib.orc_semitriangles.argtypes = [_u32p, _u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint32, ctypes.c_uint64, _u64p, _u64p, _u64p, _u64p,
                                       _u64p, _u64p, _u64p, _u64p]
+    lib.orc_mascot_stream.restype = ctypes.c_int
+    lib.orc_mascot_stream.argtypes = [_u32p, _u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                      ctypes.c_uint32, ctypes.c_uint64, _u64p, _u64p, _u64p, _u64p]
+    lib.orc_mascot_estimates.restype = None
+    lib.orc_mascot_estimates.argtypes = [ctypes.c_uint32, ctypes.c_uint32, _u64p, _u64p, ctypes.c_uint32,
+                                         _dp, _dp]
+    lib.orc_mascot_semitriangles.restype = ctypes.c_int
+    lib.orc_mascot_semitriangles.argtypes = [_u32p, _u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_uint32, ctypes.c_uint64, _u64p, _u64p, _u64p]
     return lib
 
 
@@ -174,3 +183,50 @@ def semitriangles(src, dst, n: int, m: int, c: int, seed: int, per_proc_local: b
     if rc != 0:
         raise ValueError(f"orc_semitriangles failed ({rc})")
     return Exact(tau, l1, l2, tlp, int(tt[0]), tl, int(et[0]), el)
+
+
+# --------------------------------------------------------------------------
+# parallel MASCOT (Section I, Section III-C): c independent p = 1/m samplers
+# --------------------------------------------------------------------------
+def mascot_stream(src, dst, n: int, m: int, c: int, seed: int, per_proc_local: bool = False,
+                  lib=None) -> Counts:
+    """c independent MASCOT samplers run over the stream; sampler i stores an edge iff its
+    hash-group-i colour is 0.  local1 holds sum_i tau_v^(i); local2 is zero."""
+    src, dst = _cols(src, dst)
+    lib = lib or _load()
+    tau = np.zeros(c, dtype=np.uint64)
+    l1 = np.zeros(n, dtype=np.uint64)
+    tlp = np.zeros((c, n), dtype=np.uint64) if per_proc_local else None
+    sk = np.zeros(1, dtype=np.uint64)
+    rc = lib.orc_mascot_stream(_p(src, _u32p), _p(dst, _u32p), src.size, n, m, c, seed, _p(tau, _u64p),
+                               _p(l1, _u64p), _p(tlp, _u64p), _p(sk, _u64p))
+    if rc != 0:
+        raise ValueError(f"orc_mascot_stream failed ({rc})")
+    return Counts(tau, l1, np.zeros(n, dtype=np.uint64), None, None, tlp, int(sk[0]))
+
+
+def mascot_estimates(m: int, c: int, counts: Counts, n: int, lib=None):
+    """FP64 (tau_hat, tau_hat_v[n]) of parallel MASCOT: the mean of the samplers' m^2 tau^(i)."""
+    lib = lib or _load()
+    g = np.zeros(1, dtype=np.float64)
+    loc = np.zeros(n, dtype=np.float64)
+    lib.orc_mascot_estimates(m, c, _p(np.ascontiguousarray(counts.tau_proc, dtype=np.uint64), _u64p),
+                             _p(np.ascontiguousarray(counts.local1, dtype=np.uint64), _u64p), n, _p(g, _dp),
+                             _p(loc, _dp))
+    return float(g[0]), loc
+
+
+def mascot_semitriangles(src, dst, n: int, m: int, c: int, seed: int, per_proc_local: bool = False,
+                         lib=None):
+    """Per-sampler semi-triangle counts of parallel MASCOT by static enumeration:
+    (tau_proc[c], local1[n], tau_local_proc[c, n] or None)."""
+    src, dst = _cols(src, dst)
+    lib = lib or _load()
+    tau = np.zeros(c, dtype=np.uint64)
+    l1 = np.zeros(n, dtype=np.uint64)
+    tlp = np.zeros((c, n), dtype=np.uint64) if per_proc_local else None
+    rc = lib.orc_mascot_semitriangles(_p(src, _u32p), _p(dst, _u32p), src.size, n, m, c, seed,
+                                      _p(tau, _u64p), _p(l1, _u64p), _p(tlp, _u64p))
+    if rc != 0:
+        raise ValueError(f"orc_mascot_semitriangles failed ({rc})")
+    return tau, l1, tlp

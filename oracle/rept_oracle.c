@@ -19,6 +19,9 @@
  *   orc_estimates                  the estimators of Section III-A (c <= m),
  *                                  III-B.1 (c > m, c mod m = 0) and Algorithm 2
  *                                  (c > m, c mod m != 0)
+ *   orc_mascot_stream,             parallel MASCOT (Section I, III-C): c
+ *   orc_mascot_estimates,          independent p = 1/m samplers, sampler i
+ *   orc_mascot_semitriangles       keeping h_i colour 0, estimates averaged
  *   orc_semitriangles              the definition of a semi-triangle written
  *                                  out as a static triangle enumeration: a
  *                                  triangle counts for processor i iff its two
@@ -148,14 +151,22 @@ static uint64_t edge_key(uint32_t u, uint32_t v) {
  *   skipped             self-loops seen                       (may be NULL)
  * Returns 0, or -1 on bad arguments / out of memory, -2 on an id >= n.
  */
-int orc_rept_stream(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32_t n,
-                    uint32_t m, uint32_t c, uint64_t seed,
-                    uint64_t* tau_proc, uint64_t* eta_proc,
-                    uint64_t* local1, uint64_t* local2, uint64_t* eta_local,
-                    uint64_t* tau_local_proc, uint64_t* skipped) {
+/* The processor-to-sampler map: REPT's processor i = k*m + j keeps group-k
+ * colour j; a parallel-MASCOT sampler i (Section III-C) keeps the edges whose
+ * own hash h_i colours them 0, i.e. an independent p = 1/m sample. */
+static void proc_map(int mascot, uint32_t i, uint32_t m, uint32_t* k, uint32_t* j) {
+    *k = mascot ? i : i / m;
+    *j = mascot ? 0 : i % m;
+}
+
+static int sample_stream(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32_t n,
+                         uint32_t m, uint32_t c, uint64_t seed, int mascot,
+                         uint64_t* tau_proc, uint64_t* eta_proc,
+                         uint64_t* local1, uint64_t* local2, uint64_t* eta_local,
+                         uint64_t* tau_local_proc, uint64_t* skipped) {
     if (m == 0 || c == 0 || n == 0 || !tau_proc) return -1;
     uint32_t c1 = c / m;                 /* number of full groups (0 when c < m) */
-    uint32_t full = (c <= m) ? c : c1 * m;   /* processors feeding local1 */
+    uint32_t full = (mascot || c <= m) ? c : c1 * m;   /* processors feeding local1 */
     memset(tau_proc, 0, c * sizeof(uint64_t));
     if (eta_proc) memset(eta_proc, 0, c * sizeof(uint64_t));
     if (local1) memset(local1, 0, (size_t)n * sizeof(uint64_t));
@@ -182,7 +193,8 @@ int orc_rept_stream(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32
         if (u >= n || v >= n) { rc = -2; goto done; }
         if (u == v) { if (skipped) ++*skipped; continue; }
         for (uint32_t i = 0; i < c; ++i) {
-            uint32_t k = i / m, j = i % m;
+            uint32_t k, j;
+            proc_map(mascot, i, m, &k, &j);
             /* ---- UpdateTriangleCNT(i, (u, v)): N_{u,v}^(i) = N_u^(i) cap N_v^(i) */
             uint64_t* pu = um_find(&adj_index, ((uint64_t)i << 32) | u);
             uint64_t* pv = um_find(&adj_index, ((uint64_t)i << 32) | v);
@@ -260,6 +272,28 @@ done:
     return rc;
 }
 
+int orc_rept_stream(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32_t n,
+                    uint32_t m, uint32_t c, uint64_t seed,
+                    uint64_t* tau_proc, uint64_t* eta_proc,
+                    uint64_t* local1, uint64_t* local2, uint64_t* eta_local,
+                    uint64_t* tau_local_proc, uint64_t* skipped) {
+    return sample_stream(src, dst, T, n, m, c, seed, 0, tau_proc, eta_proc, local1, local2, eta_local,
+                         tau_local_proc, skipped);
+}
+
+/*
+ * Parallel MASCOT (Section I, Section III-C): c independent edge samplers with
+ * p = 1/m, sampler i storing (u, v) iff h_i(u, v) == 0 (hash group i, colour 0),
+ * each counting like one processor of Algorithm 1.  Outputs as for
+ * orc_rept_stream; every sampler feeds local1 and local2 stays zero.
+ */
+int orc_mascot_stream(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32_t n,
+                      uint32_t m, uint32_t c, uint64_t seed,
+                      uint64_t* tau_proc, uint64_t* local1, uint64_t* tau_local_proc, uint64_t* skipped) {
+    return sample_stream(src, dst, T, n, m, c, seed, 1, tau_proc, NULL, local1, NULL, NULL, tau_local_proc,
+                         skipped);
+}
+
 /* ------------------------------------------------------------- estimators */
 
 /*
@@ -316,6 +350,23 @@ void orc_estimates(uint32_t m, uint32_t c, const uint64_t* tau_proc, const uint6
     }
 }
 
+/*
+ * Parallel MASCOT's estimates (Section I, Section III-C): the mean over the c
+ * samplers of the single-sampler estimate p^-2 tau^(i) = m^2 tau^(i), i.e.
+ * (m^2 / c) * sum_i tau^(i); the local estimates likewise from local1.
+ */
+void orc_mascot_estimates(uint32_t m, uint32_t c, const uint64_t* tau_proc, const uint64_t* local1,
+                          uint32_t n, double* est_global, double* est_local) {
+    double md = (double)m;
+    double inv_p2 = md * md;             /* one sampler's estimate is p^-2 tau^(i) */
+    double mean_f = inv_p2 / (double)c;  /* ... averaged over the c samplers */
+    uint64_t s = 0;
+    for (uint32_t i = 0; i < c; ++i) s += tau_proc[i];
+    *est_global = (double)s * mean_f;
+    if (est_local)
+        for (uint32_t v = 0; v < n; ++v) est_local[v] = (double)local1[v] * mean_f;
+}
+
 /* ------------------------------------------- static semi-triangle definition */
 
 typedef struct { uint32_t nbr, eidx; } fent;
@@ -341,16 +392,17 @@ static int fent_cmp(const void* a, const void* b) {
  * Any output pointer may be NULL.  Self-loops and repeated edges must not be
  * present (returns -3 if a repeated edge is found).
  */
-int orc_semitriangles(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32_t n,
-                      uint32_t m, uint32_t c, uint64_t seed,
-                      uint64_t* tau_proc, uint64_t* local1, uint64_t* local2,
-                      uint64_t* tau_local_proc,
-                      uint64_t* tri_total, uint64_t* tri_local,
-                      uint64_t* eta_total, uint64_t* eta_loc) {
+static int enumerate_semitriangles(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32_t n,
+                                   uint32_t m, uint32_t c, uint64_t seed, int mascot,
+                                   uint64_t* tau_proc, uint64_t* local1, uint64_t* local2,
+                                   uint64_t* tau_local_proc,
+                                   uint64_t* tri_total, uint64_t* tri_local,
+                                   uint64_t* eta_total, uint64_t* eta_loc) {
     if (n == 0 || (m == 0 && tau_proc) ) return -1;
     uint32_t c1 = m ? c / m : 0;
-    uint32_t full = (c <= m) ? c : c1 * m;
-    uint32_t groups = m ? (c + m - 1) / m : 0;
+    uint32_t full = (mascot || c <= m) ? c : c1 * m;
+    /* hash groups to classify under: one per MASCOT sampler, ceil(c/m) for REPT */
+    uint32_t groups = !m ? 0 : mascot ? c : (c + m - 1) / m;
     if (tau_proc) memset(tau_proc, 0, c * sizeof(uint64_t));
     if (local1) memset(local1, 0, (size_t)n * sizeof(uint64_t));
     if (local2) memset(local2, 0, (size_t)n * sizeof(uint64_t));
@@ -424,8 +476,8 @@ int orc_semitriangles(const uint32_t* src, const uint32_t* dst, uint64_t T, uint
                 for (uint32_t k = 0; k < groups; ++k) {
                     uint32_t j1 = orc_colour(ends[f1][0], ends[f1][1], seed, k, m);
                     uint32_t j2 = orc_colour(ends[f2][0], ends[f2][1], seed, k, m);
-                    uint32_t i = k * m + j1;
-                    if (j1 != j2 || i >= c) continue;
+                    uint32_t i = mascot ? k : k * m + j1;
+                    if (j1 != j2 || i >= c || (mascot && j1 != 0)) continue;
                     if (tau_proc) ATOMIC_INC(&tau_proc[i]);
                     uint64_t* l_sum = (i < full) ? local1 : local2;
                     if (l_sum) { ATOMIC_INC(&l_sum[x]); ATOMIC_INC(&l_sum[y]); ATOMIC_INC(&l_sum[z]); }
@@ -450,4 +502,23 @@ int orc_semitriangles(const uint32_t* src, const uint32_t* dst, uint64_t T, uint
 out:
     free(deg); free(off); free(a_g); free(fw);
     return rc;
+}
+
+int orc_semitriangles(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32_t n,
+                      uint32_t m, uint32_t c, uint64_t seed,
+                      uint64_t* tau_proc, uint64_t* local1, uint64_t* local2,
+                      uint64_t* tau_local_proc,
+                      uint64_t* tri_total, uint64_t* tri_local,
+                      uint64_t* eta_total, uint64_t* eta_loc) {
+    return enumerate_semitriangles(src, dst, T, n, m, c, seed, 0, tau_proc, local1, local2, tau_local_proc,
+                                   tri_total, tri_local, eta_total, eta_loc);
+}
+
+/* The same enumeration classified for parallel MASCOT: sampler i counts a
+ * triangle iff its two earliest edges both have h_i colour 0. */
+int orc_mascot_semitriangles(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32_t n,
+                             uint32_t m, uint32_t c, uint64_t seed,
+                             uint64_t* tau_proc, uint64_t* local1, uint64_t* tau_local_proc) {
+    return enumerate_semitriangles(src, dst, T, n, m, c, seed, 1, tau_proc, local1, NULL, tau_local_proc,
+                                   NULL, NULL, NULL, NULL);
 }

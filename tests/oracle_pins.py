@@ -48,15 +48,16 @@ def py_colour(u: int, v: int, seed: int, k: int, m: int) -> int:
     return _py_splitmix64(((lo << 32) | hi) ^ ((seed + k * GAMMA) & MASK64)) % m
 
 
-def brute_force(src, dst, n, m, c, seed):
-    """tau^(i) and tau_v^(i) by checking every node triple (n must be small)."""
+def brute_force(src, dst, n, m, c, seed, mascot=False):
+    """tau^(i) and tau_v^(i) by checking every node triple (n must be small).  With ``mascot``,
+    sampler i keeps the edges of hash group i with colour 0 (parallel MASCOT, Section III-C)."""
     when = {}
     for t, (a, b) in enumerate(zip(src.tolist(), dst.tolist())):
         if a != b:
             when[(min(a, b), max(a, b))] = t
     tau = np.zeros(c, dtype=np.uint64)
     loc = np.zeros((c, n), dtype=np.uint64)
-    groups = (c + m - 1) // m
+    groups = c if mascot else (c + m - 1) // m
     for a, b, d in itertools.combinations(range(n), 3):
         es = [(a, b), (a, d), (b, d)]
         if not all(e in when for e in es):
@@ -65,8 +66,8 @@ def brute_force(src, dst, n, m, c, seed):
         for k in range(groups):
             j1 = py_colour(*first_two[0], seed, k, m)
             j2 = py_colour(*first_two[1], seed, k, m)
-            i = k * m + j1
-            if j1 == j2 and i < c:
+            i = k if mascot else k * m + j1
+            if j1 == j2 and i < c and (j1 == 0 or not mascot):
                 tau[i] += 1
                 for x in (a, b, d):
                     loc[i, x] += 1
@@ -311,7 +312,66 @@ def pin_partial_group_statistics(lib=None):
     assert abs(eta_hats.mean() - eta) < 4.5 * eta_hats.std(ddof=1) / math.sqrt(R) + 1e-9
 
 
+def pin_mascot_brute_force(lib=None):
+    """Parallel MASCOT (Section III-C): sampler i stores an edge iff hash group i colours it 0, and
+    counts a triangle iff its two earliest edges are both stored.  The streaming and static oracles
+    equal the brute force of that definition, per sampler and node."""
+    for gi, (n, q) in enumerate([(10, 0.7), (18, 0.45)]):
+        s = gg.gnp(n, q, graph_seed=21 + gi, order_seed=8 + gi)
+        for (m, c) in [(1, 2), (2, 1), (2, 3), (3, 5), (4, 2)]:
+            for seed in (3, 1234567):
+                tau, loc = brute_force(s.src, s.dst, n, m, c, seed, mascot=True)
+                a = O.mascot_stream(s.src, s.dst, n, m, c, seed, per_proc_local=True, lib=lib)
+                t2, l2, tl2 = O.mascot_semitriangles(s.src, s.dst, n, m, c, seed, per_proc_local=True, lib=lib)
+                assert np.array_equal(a.tau_proc, tau), (n, m, c, seed, a.tau_proc, tau)
+                assert np.array_equal(a.tau_local_proc, loc), (n, m, c, seed)
+                assert np.array_equal(a.local1, loc.sum(axis=0)), (n, m, c, seed)
+                assert np.array_equal(t2, tau) and np.array_equal(tl2, loc), (n, m, c, seed)
+
+
+def pin_mascot_complete_graph(lib=None):
+    """m = 1 (p = 1): every sampler keeps every edge, so each counts all C(n,3) triangles of K_n and
+    the averaged estimate is exact."""
+    for n in (4, 9, 20):
+        s = gg.complete(n, order_seed=n + 1)
+        a = O.mascot_stream(s.src, s.dst, n, 1, 3, 5, lib=lib)
+        assert np.all(a.tau_proc == math.comb(n, 3))
+        assert np.all(a.local1 == 3 * math.comb(n - 1, 2))
+        g, loc = O.mascot_estimates(1, 3, a, n, lib=lib)
+        assert g == float(math.comb(n, 3)) and np.all(loc == float(math.comb(n - 1, 2)))
+
+
+def pin_mascot_statistics(lib=None):
+    """Section III-C: averaging c independent MASCOT samplers with p = 1/m is unbiased with variance
+    (tau(m^2-1) + 2 eta(m-1)) / c, which exceeds REPT's (tau(m^2-c) + 2 eta(m-c)) / c for
+    1 < c <= m.  400 spread hash seeds; same bands as the Theorem 3 pin."""
+    s = gg.gnp(30, 0.5, 31, 32)
+    e = O.semitriangles(s.src, s.dst, 30, 1, 1, 1, lib=lib)
+    tau, eta = e.triangles, e.eta
+    node = int(np.argmax(e.tri_local))
+    tau_v, eta_v = int(e.tri_local[node]), int(e.eta_local[node])
+    seeds = _spread_seeds(400, 3)
+    R = len(seeds)
+    for (m, c) in [(2, 1), (3, 3), (2, 4)]:
+        var = (tau * (m * m - 1) + 2 * eta * (m - 1)) / c
+        var_v = (tau_v * (m * m - 1) + 2 * eta_v * (m - 1)) / c
+        g, l = [], []
+        for seed in seeds:
+            a = O.mascot_stream(s.src, s.dst, 30, m, c, seed, lib=lib)
+            gg_, loc = O.mascot_estimates(m, c, a, 30, lib=lib)
+            g.append(gg_)
+            l.append(loc[node])
+        g, l = np.array(g), np.array(l)
+        assert abs(g.mean() - tau) < 4.5 * math.sqrt(var / R), (m, c, g.mean(), tau, var)
+        assert 0.7 < g.var(ddof=1) / var < 1.45, (m, c, g.var(ddof=1), var)
+        assert abs(l.mean() - tau_v) < 4.5 * math.sqrt(var_v / R), (m, c, l.mean(), tau_v)
+        assert 0.7 < l.var(ddof=1) / var_v < 1.45, (m, c, l.var(ddof=1), var_v)
+        if 1 < c <= m:
+            assert var > (tau * (m * m - c) + 2 * eta * (m - c)) / c
+
+
 ALL_PINS = [pin_splitmix64_published, pin_colour_uniform, pin_brute_force, pin_complete_graph,
             pin_local_sum_invariant, pin_count_before_insert, pin_self_loops, pin_networkx_triangles,
             pin_eta_exact_at_m1, pin_batch_split_and_static, pin_theorem3_statistics,
-            pin_partial_group_statistics]
+            pin_partial_group_statistics, pin_mascot_brute_force, pin_mascot_complete_graph,
+            pin_mascot_statistics]

@@ -18,12 +18,15 @@ MUTANTS = {
     "groups_share_seed": ("(uint64_t)k * 0x9E3779B97F4A7C15ULL", "(uint64_t)0"),
     "splitmix_shift": ("return z ^ (z >> 31);", "return z ^ (z >> 32);"),
     "store_wrong_colour": ("if (orc_colour(u, v, seed, k, m) == j) {", "if (orc_colour(u, v, seed, k, m) <= j) {"),
-    "slot_index_off_by_one": ("uint32_t k = i / m, j = i % m;", "uint32_t k = i / m, j = (i + 1) % m;"),
+    "slot_index_off_by_one": ("*j = mascot ? 0 : i % m;", "*j = mascot ? 0 : (i + 1) % m;"),
     "scale_m_over_c": ("double f = md * md / (double)c;", "double f = md / (double)c;"),
     "scale_full_groups": ("double f1 = md / (double)c1;", "double f1 = md * md / (double)c1;"),
     "pair_counter_starts_at_nuv": ("edge_key(u, v), 0);", "edge_key(u, v), nuv);"),
     "eta_local_u_uses_vw": ("eta_local[u] += *tuw;", "eta_local[u] += *tvw;"),
     "static_last_edge_wrong": ("if (e[q] > e[last]) last = q;", "if (e[q] < e[last]) last = q;"),
+    "mascot_samplers_share_hash": ("*k = mascot ? i : i / m;", "*k = mascot ? 0 : i / m;"),
+    "mascot_keeps_colour_i": ("*j = mascot ? 0 : i % m;", "*j = mascot ? i % m : i % m;"),
+    "mascot_scale_p_not_p2": ("double inv_p2 = md * md;", "double inv_p2 = md;"),
 }
 
 
