@@ -64,6 +64,10 @@ extern "C" {
 #define REPT_FLAG_WORK_COUNTERS 8u /* count the intersection's table reads into rept_stats (slower; not for timing) */
 #define REPT_FLAG_LOCAL_PER_PROCESSOR 16u /* also keep every tau_v^(i) (c * n_nodes uint64), read with
                                              rept_local_per_processor */
+#define REPT_FLAG_MASCOT 32u /* parallel MASCOT instead of REPT (Section I, Section III-C): c independent
+                                samplers of probability 1/m, sampler i keeping the edges that hash
+                                group i colours 0; tau^(i) as for REPT, estimates (m^2 / c) * sum,
+                                never Algorithm 2 */
 
 /* kernel ids used by rept_kernel_times */
 #define REPT_K_CLASSIFY 0

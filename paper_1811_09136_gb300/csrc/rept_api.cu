@@ -273,10 +273,11 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
     return REPT_OK;
 }
 
-// f such that tau_hat = f * (integer sum): m^2 / c for c <= m, m / c1 for c = c1 * m.
+// f such that tau_hat = f * (integer sum): m^2 / c for c <= m, m / c1 for c = c1 * m; parallel
+// MASCOT averages the samplers' m^2 tau^(i), so m^2 / c for every c.
 double estimate_factor(const rept_config& c) {
     const double md = (double)c.m;
-    if (c.c <= c.m) return md * md / (double)c.c;
+    if (c.c <= c.m || (c.flags & REPT_FLAG_MASCOT)) return md * md / (double)c.c;
     return md / (double)(c.c / c.m);
 }
 
@@ -329,7 +330,8 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
         return fail(REPT_E_CUDA);
     s->grid_intersect = s->sm_count * std::max(per_sm, 1);
     s->grid_stream = s->sm_count * 8;
-    s->groups = cfg->c <= cfg->m ? 1u : (cfg->c + cfg->m - 1) / cfg->m;
+    const bool mascot = (cfg->flags & REPT_FLAG_MASCOT) != 0;
+    s->groups = mascot ? cfg->c : cfg->c <= cfg->m ? 1u : (cfg->c + cfg->m - 1) / cfg->m;
     const uint32_t n = cfg->n_nodes;
     StreamDev& d = s->d;
     d.m = cfg->m;
@@ -351,12 +353,14 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if ((rc = dev_alloc(s, (void**)&d.pool, quads * 32ull))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&s->d_global, sizeof(double)))) return fail(rc);
     d.pool_quads = quads;
-    d.c1 = cfg->c <= cfg->m ? cfg->c : cfg->c / cfg->m;
+    d.c1 = mascot || cfg->c <= cfg->m ? cfg->c : cfg->c / cfg->m;
+    d.keep = mascot ? 1u : cfg->m;
+    d.pstride = mascot ? 1u : cfg->m;
     if (cfg->flags & REPT_FLAG_LOCAL_PER_PROCESSOR) {
         if ((rc = dev_alloc(s, (void**)&d.local_proc, (size_t)cfg->c * n * sizeof(unsigned long long))))
             return fail(rc);
     }
-    if (cfg->c > cfg->m && cfg->c % cfg->m != 0) {
+    if (!mascot && cfg->c > cfg->m && cfg->c % cfg->m != 0) {
         // Algorithm 2: the partial group's local counts and the triangle-pair counters
         if ((rc = dev_alloc(s, (void**)&d.local2, (size_t)n * sizeof(unsigned long long)))) return fail(rc);
         if ((rc = dev_alloc(s, (void**)&d.eta_proc, (size_t)cfg->c * sizeof(unsigned long long)))) return fail(rc);

@@ -140,6 +140,8 @@ struct StreamDev {
     // c > m with c mod m != 0 (Algorithm 2): the partial group's local counts and the triangle-pair
     // counters; all NULL otherwise
     uint32_t c1;                    // full groups: processors i < c1 * m feed `local`, the rest `local2`
+    uint32_t keep;                  // colours each hash group keeps: m (REPT), 1 (parallel MASCOT)
+    uint32_t pstride;               // processors per hash group: m (REPT), 1 (parallel MASCOT)
     unsigned long long* local2;     // [n_nodes] sum of tau_v^(i) over the partial group
     unsigned long long* eta_proc;   // [c] eta^(i)
     unsigned long long* eta_local;  // [n_nodes] sum over processors of eta_v^(i)
@@ -176,10 +178,17 @@ __device__ __forceinline__ uint32_t colour_of(uint32_t a, uint32_t b, uint64_t s
 __device__ __forceinline__ uint64_t group_seed(uint64_t seed, uint32_t k) { return seed + (uint64_t)k * kGoldenGamma; }
 
 // Is edge {u, v} kept by some processor (k*m + h_k(u,v) < c for some group k)?
+// The processor that keeps colour j of hash group k, if any: REPT's processor i = k*m + j (i < c);
+// parallel MASCOT's sampler i = k keeps colour 0 only (an independent p = 1/m sample per group).
+__device__ __forceinline__ bool processor_of(const StreamDev& d, uint32_t k, uint32_t j, uint32_t& i) {
+    i = k * d.pstride + j;
+    return j < d.keep && i < d.c;
+}
+
 __device__ __forceinline__ bool kept_by_any(const StreamDev& d, uint32_t u, uint32_t v) {
     for (uint32_t k = 0; k < d.groups; ++k) {
-        uint32_t j = colour_of(u, v, group_seed(d.seed, k), d.fm);
-        if (k * d.m + j < d.c) return true;
+        uint32_t i, j = colour_of(u, v, group_seed(d.seed, k), d.fm);
+        if (processor_of(d, k, j, i)) return true;
     }
     return false;
 }

@@ -378,11 +378,12 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
     for (uint32_t k = 0; k < d.groups; ++k) {
         const uint64_t sk = group_seed(d.seed, k);
         const uint32_t js = colour_of(s, w, sk, d.fm);
-        if (k * d.m + js < d.c && colour_of(l, w, sk, d.fm) == js) {
-            atomicAdd(&s_proc[k * d.m + js], 1ull);
+        uint32_t i;
+        if (processor_of(d, k, js, i) && colour_of(l, w, sk, d.fm) == js) {
+            atomicAdd(&s_proc[i], 1ull);
             if (d.local2 && k >= d.c1) ++found2; else ++found;
             if (d.local_proc) {
-                unsigned long long* lp = d.local_proc + (unsigned long long)(k * d.m + js) * d.n_nodes;
+                unsigned long long* lp = d.local_proc + (unsigned long long)i * d.n_nodes;
                 atomicAdd(&lp[s], 1ull);
                 atomicAdd(&lp[l], 1ull);
                 atomicAdd(&lp[w], 1ull);
@@ -727,9 +728,10 @@ __device__ __forceinline__ void gq_flush(const StreamDev* __restrict__ ds, Group
         for (uint32_t k = 0; k < d.groups; ++k) {
             const uint64_t sk = group_seed(d.seed, k);
             const uint32_t js = colour_of(s, w, sk, d.fm);
-            if (k * d.m + js < d.c && colour_of(l, w, sk, d.fm) == js) {
+            uint32_t i;
+            if (processor_of(d, k, js, i) && colour_of(l, w, sk, d.fm) == js) {
                 ++found;
-                atomicAdd(&d.proc[k * d.m + js], 1ull);
+                atomicAdd(&d.proc[i], 1ull);
             }
         }
         if (found) {

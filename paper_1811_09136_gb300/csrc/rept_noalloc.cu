@@ -95,6 +95,8 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
     d.m = m;
     d.c = c;
     d.groups = c <= m ? 1u : c / m;
+    d.keep = m;
+    d.pstride = m;
     d.n_nodes = n_nodes;
     d.seed = seed;
     d.fm = make_fastmod(m);

@@ -23,6 +23,7 @@ FLAG_SYNC = 2
 FLAG_PROFILE = 4
 FLAG_WORK_COUNTERS = 8
 FLAG_LOCAL_PER_PROCESSOR = 16
+FLAG_MASCOT = 32
 KERNELS = ("classify", "plan", "commit", "insert", "intersect", "estimate", "sort")
 
 

@@ -255,3 +255,25 @@ def test_snapshot_restore_resumes_exactly(m, c, flags):
     with ReptStream(s.n_nodes, m, c, 10, max_batch=4096, flags=flags) as wrong_seed:
         with pytest.raises(ReptError):
             wrong_seed.restore(snap)
+
+
+@pytest.mark.parametrize("m,c", [(1, 3), (3, 1), (4, 4), (10, 7), (4, 10), (100, 20)])
+def test_parallel_mascot_matches_oracle(m, c):
+    """FLAG_MASCOT: c independent p = 1/m samplers (hash group i, colour 0).  tau^(i), the local
+    sums, every tau_v^(i) and the (m^2/c)-scaled estimates match the oracle for several batch splits."""
+    from paper_1811_09136_gb300.rept import ReptStream, FLAG_MASCOT, FLAG_LOCAL_PER_PROCESSOR
+    s = gg.chung_lu(2500, 2.2, 20_000, graph_seed=m, order_seed=c)
+    ref = O.mascot_stream(s.src, s.dst, s.n_nodes, m, c, 17, per_proc_local=True)
+    ref_g, ref_loc = O.mascot_estimates(m, c, ref, s.n_nodes)
+    src, dst = device_edges(s)
+    for batch in (len(s), 1009):
+        with ReptStream(s.n_nodes, m, c, 17, max_batch=batch, flags=FLAG_MASCOT | FLAG_LOCAL_PER_PROCESSOR) as r:
+            for off in range(0, len(s), batch):
+                r.ingest(src[off:off + batch], dst[off:off + batch])
+            proc, local = r.counts()
+            lp = r.local_per_processor().cpu().numpy().view(np.uint64)
+            g, loc = r.estimates()
+        assert np.array_equal(proc, ref.tau_proc), (batch, proc, ref.tau_proc)
+        assert np.array_equal(local.cpu().numpy().view(np.uint64), ref.local1), batch
+        assert np.array_equal(lp, ref.tau_local_proc), batch
+        assert_estimates_close(g, loc.cpu().numpy(), ref_g, ref_loc)
