@@ -84,6 +84,17 @@ __host__ __device__ __forceinline__ uint32_t fast_mod(uint64_t x, const FastMod&
     return (uint32_t)(mulhi64(lh, (uint64_t)f.m) + ((a + b) < a ? 1u : 0u));
 }
 
+// x mod m == j for j < m, without forming the remainder: x >= j and x - j divisible by m, tested
+// as (M * (x - j) mod 2^128) < M with the same 128-bit M as fast_mod (Lemire, Kaser and Kurz,
+// "Faster remainder by direct computation", 2019: divisibility by direct computation).
+__host__ __device__ __forceinline__ bool mod_equals(uint64_t x, uint32_t j, const FastMod& f) {
+    if (f.m < 2) return j == 0u;
+    if (j >= f.m || x < j) return false;
+    const uint64_t n = x - j;
+    const uint64_t ll = f.ml * n, lh = mulhi64(f.ml, n) + f.mh * n;
+    return lh < f.mh || (lh == f.mh && ll < f.ml);
+}
+
 struct Ctrl {
     unsigned long long n_touched;   // nodes in touched[] this batch
     unsigned long long need_quads;  // table space requested by this batch, in 4-slot units
@@ -125,6 +136,9 @@ struct StreamDev {
     uint2* meta;
     uint2* pool;
     unsigned long long pool_quads;
+    // [4 * pool_quads] one byte per pool slot: for a list entry {w, t} of node x in that slot, the
+    // colour h_0(x, w).  Kept for one hash group with m <= 256 colours, else NULL.
+    uint8_t* col;
     unsigned long long* local;
     unsigned long long* proc;
     uint32_t* add;
@@ -177,6 +191,12 @@ __device__ __forceinline__ uint32_t colour_of(uint32_t a, uint32_t b, uint64_t s
 
 __device__ __forceinline__ uint64_t group_seed(uint64_t seed, uint32_t k) { return seed + (uint64_t)k * kGoldenGamma; }
 
+// h_k({a, b}) == j, for a colour j < m.
+__device__ __forceinline__ bool colour_is(uint32_t a, uint32_t b, uint64_t s_k, const FastMod& fm, uint32_t j) {
+    uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    return mod_equals(splitmix64(((lo << 32) | hi) ^ s_k), j, fm);
+}
+
 // Is edge {u, v} kept by some processor (k*m + h_k(u,v) < c for some group k)?
 // The processor that keeps colour j of hash group k, if any: REPT's processor i = k*m + j (i < c);
 // parallel MASCOT's sampler i = k keeps colour 0 only (an independent p = 1/m sample per group).
@@ -191,6 +211,15 @@ __device__ __forceinline__ bool kept_by_any(const StreamDev& d, uint32_t u, uint
         if (processor_of(d, k, j, i)) return true;
     }
     return false;
+}
+
+// With one hash group, a wedge (s, w), (l, w) can count only for the processor of colour
+// js = h_0(s, w), and only if that processor exists and h_0(l, w) = js.  The intersection reads js from
+// the colour array next to s's list and asks this of the hash alone before it probes l's table for w,
+// so all but about 1/m of the probes are skipped.
+__device__ __forceinline__ bool wedge_may_count(const StreamDev& d, uint32_t l, uint32_t w, uint32_t js) {
+    uint32_t i;
+    return processor_of(d, 0u, js, i) && colour_is(l, w, d.seed, d.fm, js);
 }
 
 // log2 of the table capacity for cnt entries: capacity = max(4, nextpow2(2*cnt)); 0 when empty.

@@ -92,15 +92,19 @@ __device__ __forceinline__ void k_plan_body(const StreamDev& d) {
 }
 
 // Move node x's entries (list of cnt_old entries at old_off) into its new block at new_off: copy the
-// list and insert each entry into the new table.  Lanes `rank` of `width` share the work.
-__device__ __forceinline__ bool move_block(uint2* pool, uint32_t old_off, uint32_t cnt_old, unsigned long long new_off,
-                                           uint32_t lg_new, uint32_t rank, uint32_t width) {
-    const uint2* old_list = pool + 4ull * old_off + (1ull << table_lg(cnt_old));
-    uint2* new_list = pool + 4ull * new_off + (1ull << lg_new);
+// list (and its colours, when kept) and insert each entry into the new table.  Lanes `rank` of
+// `width` share the work.
+__device__ __forceinline__ bool move_block(uint2* pool, uint8_t* col, uint32_t old_off, uint32_t cnt_old,
+                                           unsigned long long new_off, uint32_t lg_new, uint32_t rank, uint32_t width) {
+    const unsigned long long old_at = 4ull * old_off + (1ull << table_lg(cnt_old));
+    const unsigned long long new_at = 4ull * new_off + (1ull << lg_new);
+    const uint2* old_list = pool + old_at;
+    uint2* new_list = pool + new_at;
     bool ok = true;
     for (uint32_t j = rank; j < cnt_old; j += width) {
         const uint2 e = old_list[j];
         new_list[j] = e;
+        if (col) col[new_at + j] = col[old_at + j];
         ok &= table_insert(pool, 4ull * new_off, lg_new, e.x, e.y);
     }
     return ok;
@@ -137,7 +141,7 @@ __device__ __forceinline__ void k_commit_body(const StreamDev& d) {
                     huge = !defer;
                 } else {
                     const unsigned long long new_off = top + rel;
-                    if (!move_block(d.pool, m.x, m.y, new_off, table_lg(cnt_new), 0u, 1u))
+                    if (!move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), 0u, 1u))
                         atomicOr(&d.ctrl->status, kStInternal);
                     d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
                 }
@@ -162,7 +166,7 @@ __device__ __forceinline__ void k_rehash_big_body(const StreamDev& d) {
         const uint2 m = d.meta[x];
         const uint32_t cnt_new = m.y + d.add[x];
         const unsigned long long new_off = top + d.grow_rel[i];
-        if (!move_block(d.pool, m.x, m.y, new_off, table_lg(cnt_new), lane, 32u))
+        if (!move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), lane, 32u))
             atomicOr(&d.ctrl->status, kStInternal);
         __syncwarp();
         if (lane == 0) d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
@@ -187,7 +191,7 @@ __device__ __forceinline__ void k_rehash_huge_body(const StreamDev& d) {
         const uint2 m = d.meta[x];
         const uint32_t cnt_new = m.y + d.add[x];
         const unsigned long long new_off = top + d.grow_rel[i];
-        if (!move_block(d.pool, m.x, m.y, new_off, table_lg(cnt_new), threadIdx.x, blockDim.x)) s_bad = 1;
+        if (!move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), threadIdx.x, blockDim.x)) s_bad = 1;
         __syncthreads();
         if (threadIdx.x == 0) {
             if (s_bad) atomicOr(&d.ctrl->status, kStInternal);
@@ -234,6 +238,11 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
                 const uint32_t pu = mu.y - atomicSub(&d.add[u], 1u), pv = mv.y - atomicSub(&d.add[v], 1u);
                 d.pool[4ull * mu.x + (1ull << lu) + pu] = make_uint2(v, t);
                 d.pool[4ull * mv.x + (1ull << lv) + pv] = make_uint2(u, t);
+                if (d.col) {
+                    const uint8_t j = (uint8_t)colour_of(u, v, d.seed, d.fm);
+                    d.col[4ull * mu.x + (1ull << lu) + pu] = j;
+                    d.col[4ull * mv.x + (1ull << lv) + pv] = j;
+                }
                 if (d.edge_ends) d.edge_ends[t] = make_uint2(u, v);
             }
             // an edge can close wedges only if both endpoints have stored edges
@@ -462,9 +471,10 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
     bool has = false;
     uint32_t w = 0;
     if (valid && j < x.cnt_s) {
-        const uint2 es = d.pool[4ull * x.off_s + (1ull << (x.lgs & 0xFFu)) + j];
+        const unsigned long long at = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu)) + j;
+        const uint2 es = d.pool[at];
         if (WORK && j == 0) { wk.entries += x.cnt_s; wk.slots += x.cnt_s; }
-        if (es.y < x.t) {
+        if (es.y < x.t && (!d.col || wedge_may_count(d, x.l, es.x, d.col[at]))) {
             uint32_t nslots = 0;
             const uint32_t tl = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, es.x, nslots);
             if (WORK) { ++wk.probes; wk.pslots += nslots; }
@@ -475,10 +485,12 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
     mq_push<WORK>(d, mq, has, x.s, x.l, w, s_proc, wk);
 }
 
-// Edges whose smaller table has >= 64 slots: a warp per edge.  Each pass reads 128 slots of the
-// smaller table (two 16-byte loads per lane), packs the entries older than the edge into the warp's
-// shared-memory key queue, and then probes them with all 32 lanes.
-constexpr int kQueue = 128;
+// Edges whose smaller endpoint has more entries: a warp per edge.  Each pass reads 128 entries of
+// the smaller endpoint's list (two 16-byte loads per lane) and packs those older than the edge (and,
+// with stored colours, coloured alike for a kept processor) into the warp's shared-memory key queue.
+// The queue is probed with all 32 lanes, kProbesPerLane keys per lane, whenever it holds a full
+// round; a partial round waits for the next pass, so sparse candidates share round trips.
+constexpr int kQueue = 192;  // one partial round (< 64 keys) + 128 new keys
 #ifndef REPT_PROBES_PER_LANE
 #define REPT_PROBES_PER_LANE 2
 #endif
@@ -487,21 +499,37 @@ constexpr int kProbesPerLane = REPT_PROBES_PER_LANE;  // probes each lane keeps 
 template <bool WORK>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, unsigned long long* s_proc,
                                                uint32_t* queue, MatchQueue& mq, Work& wk) {
+    constexpr uint32_t kRound = 32u * kProbesPerLane;
+    static_assert(kRound - 1 + 128 <= kQueue, "key queue too small");
     const unsigned lane = threadIdx.x & 31u;
     const uint32_t lg_l = x.lgs >> 8, n_s = x.cnt_s;
     const unsigned long long base_l = 4ull * x.off_l;
     if (WORK && lane == 0) { wk.entries += n_s; wk.slots += n_s; }
-    // the smaller endpoint's entry list (32-byte aligned), read 128 entries per pass, two per 16-byte load
-    const uint4* list = reinterpret_cast<const uint4*>(d.pool + 4ull * x.off_s + (1ull << (x.lgs & 0xFFu)));
+    // the smaller endpoint's entry list (32-byte aligned), read 128 entries per pass, two per 16-byte
+    // load; their colours (when kept) two per 2-byte load
+    const unsigned long long at_s = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu));
+    const uint4* list = reinterpret_cast<const uint4*>(d.pool + at_s);
+    const uint16_t* cols = d.col ? reinterpret_cast<const uint16_t*>(d.col + at_s) : nullptr;
+    const uint32_t* keys_l = reinterpret_cast<const uint32_t*>(d.pool + base_l);
+    const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
+    const uint32_t cap_l = 1u << lg_l;
+    const unsigned below = (1u << lane) - 1u;
+    uint32_t n_q = 0;
     for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
-        uint32_t n_q = 0;
-        const unsigned below = (1u << lane) - 1u;
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
             const uint32_t jj = j0 + 64u * half + 2u * lane;
             uint4 q = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-            if (jj < n_s) q = list[jj >> 1];
-            const bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
+            uint32_t c2 = 0;
+            if (jj < n_s) {
+                q = list[jj >> 1];
+                if (cols) c2 = cols[jj >> 1];
+            }
+            bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
+            if (cols) {
+                a1 = a1 && wedge_may_count(d, x.l, q.x, c2 & 0xFFu);
+                a2 = a2 && wedge_may_count(d, x.l, q.z, c2 >> 8);
+            }
             const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
             if (a1) queue[n_q + __popc(m1 & below)] = q.x;
             n_q += __popc(m1);
@@ -509,12 +537,11 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
             n_q += __popc(m2);
         }
         __syncwarp();
-        // kProbesPerLane queued neighbours per lane: all their home buckets are loaded before any is
-        // examined, then the stream indices of the hits
-        const uint32_t* keys_l = reinterpret_cast<const uint32_t*>(d.pool + base_l);
-        const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
-        const uint32_t cap_l = 1u << lg_l;
-        for (uint32_t k0 = 0; k0 < n_q; k0 += 32u * kProbesPerLane) {
+        const bool last = j0 + 128u >= n_s;
+        // full rounds now, everything after the last pass: kProbesPerLane queued keys per lane, all
+        // their home buckets loaded before any is examined, then the stream indices of the hits
+        uint32_t k0 = 0;
+        for (; last ? k0 < n_q : k0 + kRound <= n_q; k0 += kRound) {
             uint32_t w[kProbesPerLane], h[kProbesPerLane], r[kProbesPerLane];
             uint4 bk[kProbesPerLane];
 #pragma unroll
@@ -545,6 +572,13 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
                 mq_push<WORK>(d, mq, w[p] != kEmptyId && r[p] < x.t, x.s, x.l, w[p], s_proc, wk);
         }
         __syncwarp();
+        if (last) break;
+        if (k0) {  // move the unprobed rest (< kRound <= k0 keys) to the front; the ranges are disjoint
+            const uint32_t rest = n_q - k0;
+            for (uint32_t r = lane; r < rest; r += 32u) queue[r] = queue[k0 + r];
+            n_q = rest;
+            __syncwarp();
+        }
     }
 }
 
@@ -808,8 +842,9 @@ __device__ __forceinline__ void group_drain_tiles(const StreamDev* __restrict__ 
                 const StreamDev& d = ds[sid];
                 x = group_item(d, cls, i - pc[sid]);
                 if (j < x.cnt_s) {
-                    const uint2 es = d.pool[4ull * x.off_s + (1ull << (x.lgs & 0xFFu)) + j];
-                    if (es.y < x.t) {
+                    const unsigned long long at = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu)) + j;
+                    const uint2 es = d.pool[at];
+                    if (es.y < x.t && (!d.col || wedge_may_count(d, x.l, es.x, d.col[at]))) {
                         uint32_t nslots = 0;
                         has = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, es.x, nslots) < x.t;
                         w = es.x;
@@ -838,7 +873,9 @@ __device__ __forceinline__ void group_drain_warps(const StreamDev* __restrict__ 
         const WorkItem x = group_item(d, cls, i - pc[sid]);
         const uint32_t lg_l = x.lgs >> 8, n_s = x.cnt_s;
         const unsigned long long base_l = 4ull * x.off_l;
-        const uint4* list = reinterpret_cast<const uint4*>(d.pool + 4ull * x.off_s + (1ull << (x.lgs & 0xFFu)));
+        const unsigned long long at_s = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu));
+        const uint4* list = reinterpret_cast<const uint4*>(d.pool + at_s);
+        const uint16_t* cols = d.col ? reinterpret_cast<const uint16_t*>(d.col + at_s) : nullptr;
         for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
             uint32_t n_q = 0;
             const unsigned below = (1u << lane) - 1u;
@@ -846,8 +883,16 @@ __device__ __forceinline__ void group_drain_warps(const StreamDev* __restrict__ 
             for (uint32_t half = 0; half < 2; ++half) {
                 const uint32_t jj = j0 + 64u * half + 2u * lane;
                 uint4 e4 = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-                if (jj < n_s) e4 = list[jj >> 1];
-                const bool a1 = jj < n_s && e4.y < x.t, a2 = jj + 1u < n_s && e4.w < x.t;
+                uint32_t c2 = 0;
+                if (jj < n_s) {
+                    e4 = list[jj >> 1];
+                    if (cols) c2 = cols[jj >> 1];
+                }
+                bool a1 = jj < n_s && e4.y < x.t, a2 = jj + 1u < n_s && e4.w < x.t;
+                if (cols) {
+                    a1 = a1 && wedge_may_count(d, x.l, e4.x, c2 & 0xFFu);
+                    a2 = a2 && wedge_may_count(d, x.l, e4.z, c2 >> 8);
+                }
                 const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
                 if (a1) queue[n_q + __popc(m1 & below)] = e4.x;
                 n_q += __popc(m1);

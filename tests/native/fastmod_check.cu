@@ -1,5 +1,5 @@
-// Host-only check of rept::fast_mod (the division-free x mod m used for the colour hash) against
-// the % operator, for edge values and 20 million pseudo-random (x, m) pairs.  Exit code 0 = all equal.
+// Host-only check of rept::fast_mod (the division-free x mod m used for the colour hash) and of
+// rept::mod_equals (the divisibility test behind the colour comparison) against the % operator, for edge values and 20 million pseudo-random (x, m) pairs.  Exit code 0 = all equal.
 #include <cstdio>
 #include <cstdint>
 #include "rept_common.cuh"
@@ -30,7 +30,28 @@ int main() {
         const rept::FastMod f = rept::make_fastmod(m);
         if (rept::fast_mod(x, f) != x % m) ++bad;
     }
+    // mod_equals(x, j) == (x % m == j) for j around the true remainder and beyond m
+    s = 2463534242ull;
+    for (long i = 0; i < 5000000; ++i) {
+        uint64_t x = xs(s);
+        if (i % 7 == 0) x >>= (i % 64);
+        uint32_t m = (uint32_t)(xs(s) >> (i % 31));
+        if (m < 2) m = 2;
+        const rept::FastMod f = rept::make_fastmod(m);
+        const uint32_t r = (uint32_t)(x % m);
+        const uint32_t js[4] = {r, r + 1u, r ? r - 1u : m - 1u, (uint32_t)(xs(s) % m)};
+        for (uint32_t j : js)
+            if (rept::mod_equals(x, j, f) != (r == j)) ++bad;
+        if (rept::mod_equals(x, m, f)) ++bad;
+    }
+    for (uint32_t m : ms) {
+        const rept::FastMod f = rept::make_fastmod(m);
+        for (uint64_t x : xs_edge)
+            for (uint32_t j = 0; j < 3 && j < m; ++j)
+                if (rept::mod_equals(x, j, f) != (x % m == j)) ++bad;
+    }
     const rept::FastMod one = rept::make_fastmod(1);
+    if (!rept::mod_equals(12345, 0, one) || rept::mod_equals(12345, 1, one)) ++bad;
     if (rept::fast_mod(12345, one) != 0) ++bad;
     std::printf("mismatches: %ld\n", bad);
     return bad != 0;
