@@ -295,7 +295,10 @@ def run_ours(args, world, rank, local, pg):
         proc_w, _ = rw.counts()
         st = rw.stats()
     assert np.array_equal(proc_w, proc), "work-counter pass disagrees with the timed pass"
-    k3_bytes = 24 * (T - st["self_loops"]) + 8 * st["small_entries"] + 8 * st["probes"] + 16 * st["counted"]
+    # per list entry scanned: 8 B {neighbour, stream index}, plus its 1-byte colour when the library
+    # keeps colours beside the lists (one hash group, 2 <= m <= 256)
+    per_entry = 8 + (1 if c <= m and 2 <= m <= 256 else 0)
+    k3_bytes = 24 * (T - st["self_loops"]) + per_entry * st["small_entries"] + 8 * st["probes"] + 16 * st["counted"]
     k3_ms, k3_n = kt["intersect"]
     k3_ms_step = k3_ms / args.steps
     peak, peak_src = hbm_peak()

@@ -50,7 +50,10 @@ constexpr unsigned kStRange = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeout
 // make this exact for every 64-bit x.
 struct FastMod {
     uint64_t mh, ml;  // M = mh * 2^64 + ml
+    uint64_t qinv;    // m = q * 2^k with q odd: q^-1 mod 2^64
+    uint64_t lim;     // floor((2^64 - 1) / m)
     uint32_t m;
+    uint32_t k;
 };
 
 __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
@@ -62,8 +65,18 @@ __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
 }
 
 inline FastMod make_fastmod(uint32_t m) {
-    FastMod f{0, 0, m};
+    FastMod f{0, 0, 0, 0, m, 0};
     if (m >= 2) {
+        // divisibility test constants: the odd part's inverse by Newton's iteration (q*q = 1 mod 8
+        // gives 3 correct bits; each step doubles them), and the largest quotient
+        uint32_t k = 0;
+        while (((m >> k) & 1u) == 0u) ++k;
+        const uint64_t q = m >> k;
+        uint64_t inv = q;
+        for (int it = 0; it < 6; ++it) inv *= 2u - q * inv;
+        f.qinv = inv;
+        f.k = k;
+        f.lim = ~0ull / m;
         // floor((2^128 - 1) / m) + 1, by long division of the all-ones 128-bit value
         const uint64_t ones = ~0ull;
         const uint64_t qh = ones / m, rh = ones % m;
@@ -84,15 +97,16 @@ __host__ __device__ __forceinline__ uint32_t fast_mod(uint64_t x, const FastMod&
     return (uint32_t)(mulhi64(lh, (uint64_t)f.m) + ((a + b) < a ? 1u : 0u));
 }
 
-// x mod m == j for j < m, without forming the remainder: x >= j and x - j divisible by m, tested
-// as (M * (x - j) mod 2^128) < M with the same 128-bit M as fast_mod (Lemire, Kaser and Kurz,
-// "Faster remainder by direct computation", 2019: divisibility by direct computation).
+// x mod m == j for j < m, without forming the remainder: x >= j and n = x - j divisible by m.  With
+// m = q * 2^k (q odd), n is a multiple of m exactly when (n * q^-1 mod 2^64) rotated right by k is at
+// most floor((2^64 - 1) / m) (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994, Section 9): one 64-bit multiply instead of a remainder.
 __host__ __device__ __forceinline__ bool mod_equals(uint64_t x, uint32_t j, const FastMod& f) {
     if (f.m < 2) return j == 0u;
     if (j >= f.m || x < j) return false;
-    const uint64_t n = x - j;
-    const uint64_t ll = f.ml * n, lh = mulhi64(f.ml, n) + f.mh * n;
-    return lh < f.mh || (lh == f.mh && ll < f.ml);
+    const uint64_t y = (x - j) * f.qinv;
+    const uint64_t r = (y >> f.k) | (y << ((64u - f.k) & 63u));
+    return r <= f.lim;
 }
 
 struct Ctrl {
