@@ -490,6 +490,14 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
 // with stored colours, coloured alike for a kept processor) into the warp's shared-memory key queue.
 // The queue is probed with all 32 lanes, kProbesPerLane keys per lane, whenever it holds a full
 // round; a partial round waits for the next pass, so sparse candidates share round trips.
+#ifndef REPT_GRAB_MID
+#define REPT_GRAB_MID 4
+#endif
+#ifndef REPT_GRAB_HUB
+#define REPT_GRAB_HUB 2
+#endif
+constexpr uint32_t kGrabMid = REPT_GRAB_MID;  // class 4 items (33..256 entries) claimed per atomic
+constexpr uint32_t kGrabHub = REPT_GRAB_HUB;  // class 5 items (more entries) claimed per atomic
 constexpr int kQueue = 192;  // one partial round (< 64 keys) + 128 new keys
 #ifndef REPT_PROBES_PER_LANE
 #define REPT_PROBES_PER_LANE 2
@@ -514,17 +522,32 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
     const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
     const uint32_t cap_l = 1u << lg_l;
     const unsigned below = (1u << lane) - 1u;
-    uint32_t n_q = 0;
-    for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
+    // the next pass's entries and colours are loaded while the current pass is tested
+    uint4 nq[2];
+    uint32_t nc[2];
+    auto load_pass = [&](uint32_t j0) {
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
             const uint32_t jj = j0 + 64u * half + 2u * lane;
-            uint4 q = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-            uint32_t c2 = 0;
+            nq[half] = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
+            nc[half] = 0u;
             if (jj < n_s) {
-                q = list[jj >> 1];
-                if (cols) c2 = cols[jj >> 1];
+                nq[half] = list[jj >> 1];
+                if (cols) nc[half] = cols[jj >> 1];
             }
+        }
+    };
+    load_pass(0u);
+    uint32_t n_q = 0;
+    for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
+        const uint4 cq[2] = {nq[0], nq[1]};
+        const uint32_t cc[2] = {nc[0], nc[1]};
+        if (j0 + 128u < n_s) load_pass(j0 + 128u);
+#pragma unroll
+        for (uint32_t half = 0; half < 2; ++half) {
+            const uint32_t jj = j0 + 64u * half + 2u * lane;
+            const uint4 q = cq[half];
+            const uint32_t c2 = cc[half];
             bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
             if (cols) {
                 a1 = a1 && wedge_may_count(d, x.l, q.x, c2 & 0xFFu);
@@ -605,19 +628,24 @@ __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, int cls, unsi
     }
 }
 
+// Warp classes: a warp claims `grab` consecutive items per atomic on the class cursor (one cursor is
+// shared by every warp of the grid, so claiming one item at a time serialises on it).
 template <bool WORK>
-__device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, unsigned long long* s_proc,
+__device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint32_t grab, unsigned long long* s_proc,
                                                uint32_t* queue, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long count = d.ctrl->bin_count[cls];
     const WorkItem* items = d.srec + d.ctrl->bin_start[cls];
     for (;;) {
-        unsigned long long i = 0;
-        if (lane == 0) i = atomicAdd(&d.ctrl->bin_next[cls], 1ull);
-        i = __shfl_sync(0xFFFFFFFFu, i, 0);
-        if (i >= count) break;
-        const WorkItem x = items[i];
-        intersect_warp<WORK>(d, x, s_proc, queue, mq, wk);
+        unsigned long long i0 = 0;
+        if (lane == 0) i0 = atomicAdd(&d.ctrl->bin_next[cls], (unsigned long long)grab);
+        i0 = __shfl_sync(0xFFFFFFFFu, i0, 0);
+        if (i0 >= count) break;
+        const unsigned long long i1 = i0 + grab < count ? i0 + grab : count;
+        for (unsigned long long i = i0; i < i1; ++i) {
+            const WorkItem x = items[i];
+            intersect_warp<WORK>(d, x, s_proc, queue, mq, wk);
+        }
     }
 }
 
@@ -654,9 +682,9 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
                 p0 = p1;
             }
         };
-        drain_warp_bin<WORK>(d, 5, s_proc, queue, mq, wk);
+        drain_warp_bin<WORK>(d, 5, kGrabHub, s_proc, queue, mq, wk);
         mark(5);
-        drain_warp_bin<WORK>(d, 4, s_proc, queue, mq, wk);
+        drain_warp_bin<WORK>(d, 4, kGrabMid, s_proc, queue, mq, wk);
         mark(4);
         drain_tile_bin<32, WORK>(d, 3, s_proc, mq, wk);
         mark(3);
@@ -1093,7 +1121,7 @@ __global__ void k_sort_scatter_multi(const StreamDev* __restrict__ ds, const Bat
 }
 
 template <bool WORK>
-__global__ void __launch_bounds__(256, 8) k_intersect(StreamDev d, BatchDev b) { k_intersect_body<WORK>(d, b); }
+__global__ void __launch_bounds__(256, 5) k_intersect(StreamDev d, BatchDev b) { k_intersect_body<WORK>(d, b); }
 
 template <bool WORK>
 __global__ void __launch_bounds__(256, 8) k_intersect_multi(const StreamDev* __restrict__ ds,
