@@ -1124,7 +1124,7 @@ template <bool WORK>
 __global__ void __launch_bounds__(256, 5) k_intersect(StreamDev d, BatchDev b) { k_intersect_body<WORK>(d, b); }
 
 template <bool WORK>
-__global__ void __launch_bounds__(256, 8) k_intersect_multi(const StreamDev* __restrict__ ds,
+__global__ void __launch_bounds__(256, 5) k_intersect_multi(const StreamDev* __restrict__ ds,
                                                              const BatchDev* __restrict__ bs) {
     __shared__ StreamDev sd;
     __shared__ BatchDev sb;
