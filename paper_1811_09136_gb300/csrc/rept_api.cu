@@ -268,10 +268,16 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
     const unsigned long long want_i = (n * 8 + 255) / 256;  // work is claimed dynamically; >= 1 block
     const int grid_i = (int)std::min<unsigned long long>(want_i, (unsigned long long)s->grid_intersect);
     const size_t smem = s->cfg.c * sizeof(unsigned long long);
-    if (s->cfg.flags & REPT_FLAG_WORK_COUNTERS)
-        rc = timed_launch(s, REPT_K_INTERSECT, st, [&] { k_intersect<true><<<grid_i, 256, smem, st>>>(s->d, b); });
-    else
-        rc = timed_launch(s, REPT_K_INTERSECT, st, [&] { k_intersect<false><<<grid_i, 256, smem, st>>>(s->d, b); });
+    const bool work = (s->cfg.flags & REPT_FLAG_WORK_COUNTERS) != 0;
+    rc = timed_launch(s, REPT_K_INTERSECT, st, [&] {
+        if (s->d.col) {
+            if (work) k_intersect<true><<<grid_i, 256, smem, st>>>(s->d, b);
+            else k_intersect<false><<<grid_i, 256, smem, st>>>(s->d, b);
+        } else {
+            if (work) k_intersect_probe<true><<<grid_i, 256, smem, st>>>(s->d, b);
+            else k_intersect_probe<false><<<grid_i, 256, smem, st>>>(s->d, b);
+        }
+    });
     if (rc) return rc;
     if (s->d.pair_tau &&
         (rc = timed_launch(s, REPT_K_INTERSECT, st, [&] { k_pairs<<<s->sm_count * 4, 256, 0, st>>>(s->d); })))
@@ -331,9 +337,13 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if (cudaGetDevice(&s->device) != cudaSuccess) return fail(REPT_E_CUDA);
     if (cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess)
         return fail(REPT_E_CUDA);
+    // the intersection grid: as many blocks as fit at once, for the variant this stream uses
+    const bool coloured = (cfg->flags & REPT_FLAG_MASCOT ? cfg->c : (cfg->c + cfg->m - 1) / cfg->m) == 1 &&
+                          cfg->m >= 2 && cfg->m <= 256;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_intersect<false>, 256,
-                                                      cfg->c * sizeof(unsigned long long)) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coloured ? (const void*)k_intersect<false>
+                                                                        : (const void*)k_intersect_probe<false>,
+                                                      256, cfg->c * sizeof(unsigned long long)) != cudaSuccess)
         return fail(REPT_E_CUDA);
     s->grid_intersect = s->sm_count * std::max(per_sm, 1);
     s->grid_stream = s->sm_count * 8;
@@ -361,7 +371,7 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if ((rc = dev_alloc(s, (void**)&s->d_global, sizeof(double)))) return fail(rc);
     d.pool_quads = quads;
     // one hash group with few colours: keep each list entry's colour beside it (one byte per slot)
-    if (s->groups == 1 && cfg->m >= 2 && cfg->m <= 256) {
+    if (coloured) {
         if ((rc = dev_alloc(s, (void**)&d.col, quads * 4ull))) return fail(rc);
     }
     d.c1 = mascot || cfg->c <= cfg->m ? cfg->c : cfg->c / cfg->m;

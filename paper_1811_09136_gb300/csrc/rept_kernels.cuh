@@ -494,7 +494,7 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
 #define REPT_GRAB_MID 4
 #endif
 #ifndef REPT_GRAB_HUB
-#define REPT_GRAB_HUB 2
+#define REPT_GRAB_HUB 1
 #endif
 constexpr uint32_t kGrabMid = REPT_GRAB_MID;  // class 4 items (33..256 entries) claimed per atomic
 constexpr uint32_t kGrabHub = REPT_GRAB_HUB;  // class 5 items (more entries) claimed per atomic
@@ -504,7 +504,9 @@ constexpr int kQueue = 192;  // one partial round (< 64 keys) + 128 new keys
 #endif
 constexpr int kProbesPerLane = REPT_PROBES_PER_LANE;  // probes each lane keeps in flight (warp path)
 
-template <bool WORK>
+// COLOURED: the variant for streams that keep colours (hash-bound; the next pass is prefetched); the
+// other variant serves streams without them (probe-bound; fewer registers, more warps per SM).
+template <bool WORK, bool COLOURED>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, unsigned long long* s_proc,
                                                uint32_t* queue, MatchQueue& mq, Work& wk) {
     constexpr uint32_t kRound = 32u * kProbesPerLane;
@@ -517,12 +519,12 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
     // load; their colours (when kept) two per 2-byte load
     const unsigned long long at_s = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu));
     const uint4* list = reinterpret_cast<const uint4*>(d.pool + at_s);
-    const uint16_t* cols = d.col ? reinterpret_cast<const uint16_t*>(d.col + at_s) : nullptr;
+    const uint16_t* cols = COLOURED && d.col ? reinterpret_cast<const uint16_t*>(d.col + at_s) : nullptr;
     const uint32_t* keys_l = reinterpret_cast<const uint32_t*>(d.pool + base_l);
     const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
     const uint32_t cap_l = 1u << lg_l;
     const unsigned below = (1u << lane) - 1u;
-    // the next pass's entries and colours are loaded while the current pass is tested
+    // COLOURED: the next pass's entries and colours are loaded while the current pass is tested
     uint4 nq[2];
     uint32_t nc[2];
     auto load_pass = [&](uint32_t j0) {
@@ -537,19 +539,20 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
             }
         }
     };
-    load_pass(0u);
+    if (COLOURED) load_pass(0u);
     uint32_t n_q = 0;
     for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
+        if (!COLOURED) load_pass(j0);
         const uint4 cq[2] = {nq[0], nq[1]};
         const uint32_t cc[2] = {nc[0], nc[1]};
-        if (j0 + 128u < n_s) load_pass(j0 + 128u);
+        if (COLOURED && j0 + 128u < n_s) load_pass(j0 + 128u);
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
             const uint32_t jj = j0 + 64u * half + 2u * lane;
             const uint4 q = cq[half];
             const uint32_t c2 = cc[half];
             bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
-            if (cols) {
+            if (COLOURED && cols) {
                 a1 = a1 && wedge_may_count(d, x.l, q.x, c2 & 0xFFu);
                 a2 = a2 && wedge_may_count(d, x.l, q.z, c2 >> 8);
             }
@@ -630,7 +633,7 @@ __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, int cls, unsi
 
 // Warp classes: a warp claims `grab` consecutive items per atomic on the class cursor (one cursor is
 // shared by every warp of the grid, so claiming one item at a time serialises on it).
-template <bool WORK>
+template <bool WORK, bool COLOURED>
 __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint32_t grab, unsigned long long* s_proc,
                                                uint32_t* queue, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
@@ -644,7 +647,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint
         const unsigned long long i1 = i0 + grab < count ? i0 + grab : count;
         for (unsigned long long i = i0; i < i1; ++i) {
             const WorkItem x = items[i];
-            intersect_warp<WORK>(d, x, s_proc, queue, mq, wk);
+            intersect_warp<WORK, COLOURED>(d, x, s_proc, queue, mq, wk);
         }
     }
 }
@@ -652,7 +655,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint
 // UpdateTriangleCNT for every edge of the batch.  The edges were sorted into work classes by
 // k_insert; warps claim work dynamically, largest class first.  Dynamic shared memory: c uint64
 // counters (tau^(i) of this block).  WORK = true also tallies the table reads.
-template <bool WORK>
+template <bool WORK, bool COLOURED>
 __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const BatchDev& b) {
     extern __shared__ unsigned long long s_proc[];
     __shared__ uint32_t s_queue[256 / 32][kQueue];
@@ -682,9 +685,9 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
                 p0 = p1;
             }
         };
-        drain_warp_bin<WORK>(d, 5, kGrabHub, s_proc, queue, mq, wk);
+        drain_warp_bin<WORK, COLOURED>(d, 5, kGrabHub, s_proc, queue, mq, wk);
         mark(5);
-        drain_warp_bin<WORK>(d, 4, kGrabMid, s_proc, queue, mq, wk);
+        drain_warp_bin<WORK, COLOURED>(d, 4, kGrabMid, s_proc, queue, mq, wk);
         mark(4);
         drain_tile_bin<32, WORK>(d, 3, s_proc, mq, wk);
         mark(3);
@@ -1120,8 +1123,16 @@ __global__ void k_sort_scatter_multi(const StreamDev* __restrict__ ds, const Bat
     k_sort_scatter_body(sd, sb);
 }
 
+// Streams that keep colours (one hash group, m <= 256): 5 blocks of 256 threads per SM.
 template <bool WORK>
-__global__ void __launch_bounds__(256, 5) k_intersect(StreamDev d, BatchDev b) { k_intersect_body<WORK>(d, b); }
+__global__ void __launch_bounds__(256, 5) k_intersect(StreamDev d, BatchDev b) { k_intersect_body<WORK, true>(d, b); }
+
+// Streams without colours (several hash groups or m > 256): every probe is issued, so the kernel
+// waits on memory and wants every warp an SM can hold.
+template <bool WORK>
+__global__ void __launch_bounds__(256, 8) k_intersect_probe(StreamDev d, BatchDev b) {
+    k_intersect_body<WORK, false>(d, b);
+}
 
 template <bool WORK>
 __global__ void __launch_bounds__(256, 5) k_intersect_multi(const StreamDev* __restrict__ ds,
@@ -1133,7 +1144,7 @@ __global__ void __launch_bounds__(256, 5) k_intersect_multi(const StreamDev* __r
         sb = bs[blockIdx.y];
     }
     __syncthreads();
-    k_intersect_body<WORK>(sd, sb);
+    k_intersect_body<WORK, true>(sd, sb);
 }
 
 // tau_hat_v = f * sum_i tau_v^(i), f formed in double on the host.

@@ -142,7 +142,7 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
         k_sort_scatter<<<grid, threads, 0, st>>>(d, b);
         const unsigned long long want_i = (n_edges * 8 + 255) / 256;
         const int grid_i = (int)(want_i < (unsigned long long)sms * 4 ? want_i : (unsigned long long)sms * 4);
-        k_intersect<false><<<grid_i, 256, c * sizeof(unsigned long long), st>>>(d, b);
+        k_intersect_probe<false><<<grid_i, 256, c * sizeof(unsigned long long), st>>>(d, b);
         NA_CUDA(cudaPeekAtLastError());
     }
     if (d_global) {
