@@ -506,9 +506,10 @@ constexpr int kProbesPerLane = REPT_PROBES_PER_LANE;  // probes each lane keeps 
 
 // COLOURED: the variant for streams that keep colours (hash-bound; the next pass is prefetched); the
 // other variant serves streams without them (probe-bound; fewer registers, more warps per SM).
-template <bool WORK, bool COLOURED>
-__device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, unsigned long long* s_proc,
-                                               uint32_t* queue, MatchQueue& mq, Work& wk) {
+// `push(has, w)` (warp-collective) takes each probed key w and whether it closed a wedge.
+template <bool WORK, bool COLOURED, class Push>
+__device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, uint32_t* queue, Work& wk,
+                                               Push&& push) {
     constexpr uint32_t kRound = 32u * kProbesPerLane;
     static_assert(kRound - 1 + 128 <= kQueue, "key queue too small");
     const unsigned lane = threadIdx.x & 31u;
@@ -595,7 +596,7 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
             }
 #pragma unroll
             for (int p = 0; p < kProbesPerLane; ++p)
-                mq_push<WORK>(d, mq, w[p] != kEmptyId && r[p] < x.t, x.s, x.l, w[p], s_proc, wk);
+                push(w[p] != kEmptyId && r[p] < x.t, w[p]);
         }
         __syncwarp();
         if (last) break;
@@ -647,7 +648,9 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint
         const unsigned long long i1 = i0 + grab < count ? i0 + grab : count;
         for (unsigned long long i = i0; i < i1; ++i) {
             const WorkItem x = items[i];
-            intersect_warp<WORK, COLOURED>(d, x, s_proc, queue, mq, wk);
+            intersect_warp<WORK, COLOURED>(d, x, queue, wk, [&](bool has, uint32_t w) {
+                mq_push<WORK>(d, mq, has, x.s, x.l, w, s_proc, wk);
+            });
         }
     }
 }
@@ -887,66 +890,33 @@ __device__ __forceinline__ void group_drain_tiles(const StreamDev* __restrict__ 
     }
 }
 
-__device__ __forceinline__ void group_drain_warps(const StreamDev* __restrict__ ds, uint32_t k, int cls,
+__device__ __forceinline__ void group_drain_warps(const StreamDev* __restrict__ ds, uint32_t k, int cls, uint32_t grab,
                                                   const unsigned long long* __restrict__ pref,
                                                   unsigned long long* __restrict__ cursor, uint32_t* queue,
                                                   GroupQueue& q) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long* pc = pref + cls * (k + 1);
     const unsigned long long total = pc[k];
+    Work wk;  // not tallied on this path
     for (;;) {
-        unsigned long long i = 0;
-        if (lane == 0) i = atomicAdd(&cursor[cls], 1ull);
-        i = __shfl_sync(0xFFFFFFFFu, i, 0);
-        if (i >= total) break;
-        const uint32_t sid = group_stream_search(pc, k, i);
-        const StreamDev& d = ds[sid];
-        const WorkItem x = group_item(d, cls, i - pc[sid]);
-        const uint32_t lg_l = x.lgs >> 8, n_s = x.cnt_s;
-        const unsigned long long base_l = 4ull * x.off_l;
-        const unsigned long long at_s = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu));
-        const uint4* list = reinterpret_cast<const uint4*>(d.pool + at_s);
-        const uint16_t* cols = d.col ? reinterpret_cast<const uint16_t*>(d.col + at_s) : nullptr;
-        for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
-            uint32_t n_q = 0;
-            const unsigned below = (1u << lane) - 1u;
-#pragma unroll
-            for (uint32_t half = 0; half < 2; ++half) {
-                const uint32_t jj = j0 + 64u * half + 2u * lane;
-                uint4 e4 = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-                uint32_t c2 = 0;
-                if (jj < n_s) {
-                    e4 = list[jj >> 1];
-                    if (cols) c2 = cols[jj >> 1];
-                }
-                bool a1 = jj < n_s && e4.y < x.t, a2 = jj + 1u < n_s && e4.w < x.t;
-                if (cols) {
-                    a1 = a1 && wedge_may_count(d, x.l, e4.x, c2 & 0xFFu);
-                    a2 = a2 && wedge_may_count(d, x.l, e4.z, c2 >> 8);
-                }
-                const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
-                if (a1) queue[n_q + __popc(m1 & below)] = e4.x;
-                n_q += __popc(m1);
-                if (a2) queue[n_q + __popc(m2 & below)] = e4.z;
-                n_q += __popc(m2);
-            }
-            __syncwarp();
-            for (uint32_t k0 = 0; k0 < n_q; k0 += 32u) {
-                bool has = false;
-                uint32_t w = 0;
-                if (k0 + lane < n_q) {
-                    w = queue[k0 + lane];
-                    uint32_t nslots = 0;
-                    has = table_find(d.pool, base_l, lg_l, w, nslots) < x.t;
-                }
+        unsigned long long i0 = 0;
+        if (lane == 0) i0 = atomicAdd(&cursor[cls], (unsigned long long)grab);
+        i0 = __shfl_sync(0xFFFFFFFFu, i0, 0);
+        if (i0 >= total) break;
+        const unsigned long long i1 = i0 + grab < total ? i0 + grab : total;
+        uint32_t sid = group_stream_search(pc, k, i0);
+        for (unsigned long long i = i0; i < i1; ++i) {
+            sid = group_stream_of(pc, k, i, sid);
+            const StreamDev& d = ds[sid];
+            const WorkItem x = group_item(d, cls, i - pc[sid]);
+            intersect_warp<false, true>(d, x, queue, wk, [&](bool has, uint32_t w) {
                 gq_push(ds, q, has, sid, x.s, x.l, w);
-            }
-            __syncwarp();
+            });
         }
     }
 }
 
-__global__ void __launch_bounds__(256, 5) k_intersect_group(const StreamDev* __restrict__ ds, uint32_t k,
+__global__ void __launch_bounds__(256, 4) k_intersect_group(const StreamDev* __restrict__ ds, uint32_t k,
                                                             const unsigned long long* __restrict__ pref,
                                                             unsigned long long* __restrict__ cursor) {
     __shared__ uint32_t s_queue[256 / 32][kQueue];
@@ -954,8 +924,8 @@ __global__ void __launch_bounds__(256, 5) k_intersect_group(const StreamDev* __r
     const unsigned wid = threadIdx.x >> 5;
     uint32_t* queue = s_queue[wid];
     GroupQueue q{s_match[wid][0], s_match[wid][1], s_match[wid][2], s_match[wid][3], 0u};
-    group_drain_warps(ds, k, 5, pref, cursor, queue, q);
-    group_drain_warps(ds, k, 4, pref, cursor, queue, q);
+    group_drain_warps(ds, k, 5, kGrabHub, pref, cursor, queue, q);
+    group_drain_warps(ds, k, 4, kGrabMid, pref, cursor, queue, q);
     group_drain_tiles<32>(ds, k, 3, pref, cursor, q);
     group_drain_tiles<16>(ds, k, 2, pref, cursor, q);
     group_drain_tiles<8>(ds, k, 1, pref, cursor, q);
