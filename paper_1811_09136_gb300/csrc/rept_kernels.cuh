@@ -26,17 +26,26 @@ namespace {
 // (keys; probed a 4-key, 16-byte bucket at a time) and then, at the same positions, the stream index
 // of each entry.  Insert (nbr, eidx): claim a key slot with a 32-bit CAS, then store the index.
 // Returns false only if the table has no empty slot left (impossible while cnt <= capacity / 2).
+// Lookups read whole 4-key buckets, so where a key sits inside its bucket does not matter: an insert
+// tries the slots of a bucket starting from one chosen by other bits of the key, so that keys sharing
+// a home bucket seldom contend for the same slot, and moves to the next bucket only when all four are
+// taken.
 __device__ __forceinline__ bool table_insert(uint2* pool, unsigned long long base, uint32_t lg, uint32_t nbr,
                                              uint32_t eidx) {
     uint32_t* keys = reinterpret_cast<uint32_t*>(pool + base);
     const uint32_t mask = (1u << lg) - 1u;
-    uint32_t h = home_slot(nbr, lg);
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        if (atomicCAS(keys + h, kEmptyId, nbr) == kEmptyId) {
-            keys[(1u << lg) + h] = eidx;
-            return true;
+    const uint32_t start = (nbr * 0x85EBCA6Bu) >> 30;
+    uint32_t b = home_slot(nbr, lg);
+    for (uint32_t probe = 0; probe <= mask; probe += 4u) {
+#pragma unroll
+        for (uint32_t i = 0; i < 4u; ++i) {
+            const uint32_t h = b + ((start + i) & 3u);
+            if (atomicCAS(keys + h, kEmptyId, nbr) == kEmptyId) {
+                keys[(1u << lg) + h] = eidx;
+                return true;
+            }
         }
-        h = (h + 1u) & mask;
+        b = (b + 4u) & mask;
     }
     return false;
 }
