@@ -57,6 +57,7 @@ extern "C" {
 #define REPT_E_TIMEOUT (-6)   /* a bounded device-side wait gave up (batched persistent path) */
 #define REPT_E_INTERNAL (-7)  /* a device-side invariant failed (bounded probe found no slot) */
 #define REPT_E_SCRATCH (-8)   /* rept_count_noalloc: the problem does not fit its fixed scratch area */
+#define REPT_E_DUPLICATE (-9) /* REPT_FLAG_CHECK_DUPS: a repeated edge (device-detected, batch not applied) */
 
 #define REPT_FLAG_FIXED_POOL 1u /* never grow the adjacency pool; a full pool gives REPT_E_CAPACITY */
 #define REPT_FLAG_SYNC 2u       /* synchronise at the end of every ingest and report errors at once */
@@ -68,6 +69,11 @@ extern "C" {
                                 samplers of probability 1/m, sampler i keeping the edges that hash
                                 group i colours 0; tau^(i) as for REPT, estimates (m^2 / c) * sum,
                                 never Algorithm 2 */
+#define REPT_FLAG_CHECK_DUPS 64u /* debug: before a batch is applied, look for an edge that repeats a stored
+                                    edge or another edge of the same batch (E is a set, Section II; a
+                                    repeat is a caller error) and fail the batch with REPT_E_DUPLICATE.
+                                    A repeat of an earlier edge that no processor stored is not seen.
+                                    Checked by rept_ingest_batch / rept_ingest_host, not by group ingest */
 
 /* kernel ids used by rept_kernel_times */
 #define REPT_K_CLASSIFY 0
@@ -287,6 +293,17 @@ int rept_group_ingest(rept_group* g, rept_state* const* hs, const uint32_t* cons
 
 /* rept_group_destroy: release the group (not the handles).  NULL is a no-op. */
 void rept_group_destroy(rept_group* g);
+
+/*
+ * rept_ingest_multi: rept_group_ingest through a group that the library
+ * keeps for the current device, for callers that do not want to manage one:
+ * the same arguments, counts and errors.  The group is made on the first call
+ * (sized for max(k, 64) streams), made again, larger, when a call brings more
+ * streams (that call synchronises the device), and kept until the process
+ * exits.  Calls from several host threads are serialised.
+ */
+int rept_ingest_multi(rept_state* const* hs, const uint32_t* const* d_src, const uint32_t* const* d_dst,
+                      const uint64_t* n, uint32_t k, void* stream);
 
 /*
  * rept_count_noalloc: count a whole edge stream in one call without

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "rept.h"
@@ -47,6 +48,7 @@ int status_to_code(unsigned st) {
     if (st & kStCapacity) return REPT_E_CAPACITY;
     if (st & kStTimeout) return REPT_E_TIMEOUT;
     if (st & kStInternal) return REPT_E_INTERNAL;
+    if (st & kStDuplicate) return REPT_E_DUPLICATE;
     return REPT_OK;
 }
 
@@ -243,6 +245,15 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
     int rc = REPT_OK;
     if ((rc = timed_launch(s, REPT_K_CLASSIFY, st, [&] { k_classify<<<grid, threads, 0, st>>>(s->d, b); })))
         return rc;
+    if (s->cfg.flags & REPT_FLAG_CHECK_DUPS) {
+        // the set of this batch's edge keys: a power of two >= 2n slots of 8 bytes in the work-record
+        // scratch (32 bytes per batch edge, so at most half of it)
+        unsigned long long cap = 1;
+        while (cap < 2 * n) cap <<= 1;
+        REPT_CUDA(cudaMemsetAsync(s->d.rec, 0xFF, cap * sizeof(unsigned long long), st));
+        if ((rc = timed_launch(s, REPT_K_CLASSIFY, st, [&] { k_check_dups<<<grid, threads, 0, st>>>(s->d, b, cap - 1); })))
+            return rc;
+    }
     if ((rc = timed_launch(s, REPT_K_PLAN, st, [&] { k_plan<<<grid, threads, 0, st>>>(s->d); }))) return rc;
     const bool fixed = (s->cfg.flags & REPT_FLAG_FIXED_POOL) != 0;
     if (!fixed && s->d.pool_quads < quads_bound(s->next_t + n)) {
@@ -1038,6 +1049,32 @@ int rept_group_ingest(rept_group* g, rept_state* const* hs, const uint32_t* cons
     return REPT_OK;
 }
 
+// rept_ingest_multi: one library-owned group per device, grown (recreated) when a call brings more
+// streams than it was made for.
+namespace {
+std::mutex g_multi_lock;
+std::vector<rept_group*> g_multi_groups;  // indexed by device
+}  // namespace
+
+int rept_ingest_multi(rept_state* const* hs, const uint32_t* const* d_src, const uint32_t* const* d_dst,
+                      const uint64_t* n, uint32_t k, void* stream) {
+    if (!hs || !d_src || !d_dst || !n || k == 0) return REPT_E_INVAL;
+    int dev = 0;
+    REPT_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_multi_lock);
+    if ((size_t)dev >= g_multi_groups.size()) g_multi_groups.resize((size_t)dev + 1, nullptr);
+    rept_group*& g = g_multi_groups[(size_t)dev];
+    if (g && g->max_streams < k) {
+        rept_group_destroy(g);
+        g = nullptr;
+    }
+    if (!g) {
+        const int rc = rept_group_create(std::max<uint32_t>(k, 64u), 0u, &g);
+        if (rc) return rc;
+    }
+    return rept_group_ingest(g, hs, d_src, d_dst, n, k, stream);
+}
+
 const char* rept_strerror(int code) {
     switch (code) {
         case REPT_OK: return "ok";
@@ -1049,6 +1086,7 @@ const char* rept_strerror(int code) {
         case REPT_E_TIMEOUT: return "bounded device wait timed out";
         case REPT_E_INTERNAL: return "internal device invariant failed";
         case REPT_E_SCRATCH: return "problem exceeds the fixed scratch area of rept_count_noalloc";
+        case REPT_E_DUPLICATE: return "repeated edge in the stream (REPT_FLAG_CHECK_DUPS)";
         default: return "unknown error";
     }
 }

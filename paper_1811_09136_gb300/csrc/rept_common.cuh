@@ -42,7 +42,7 @@ constexpr uint32_t kSortBuckets = kBins * kKeyBuckets;
 constexpr uint16_t kNoKey = 0xFFFFu;
 
 // status bits (sticky)
-constexpr unsigned kStRange = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeout = 8u;
+constexpr unsigned kStRange = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeout = 8u, kStDuplicate = 16u;
 
 // x mod m for 64-bit x and 32-bit m >= 2 without a division: Lemire, Kaser, Kurz, "Faster Remainder
 // by Direct Computation" (2019).  With the 128-bit magic M = floor((2^128 - 1) / m) + 1, the low 128

@@ -375,6 +375,33 @@ __device__ __forceinline__ uint32_t table_find(const uint2* __restrict__ pool, u
     return kEmptyId;
 }
 
+// REPT_FLAG_CHECK_DUPS: before the batch is applied, flag an edge that repeats an earlier stored
+// edge (found in its endpoint's table) or another edge of the same batch (found in a set of the
+// batch's edge keys, built in the work-record scratch, which is free at this point and was filled
+// with ~0 by the host).  `mask` + 1 is the set's capacity, a power of two at least twice the batch.
+__global__ void k_check_dups(StreamDev d, BatchDev b, unsigned long long mask) {
+    if (d.ctrl->status) return;
+    unsigned long long* set = reinterpret_cast<unsigned long long*>(d.rec);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    bool dup = false;
+    for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.n; e += stride) {
+        const uint32_t u = b.src[e], v = b.dst[e];
+        if (u == v || u >= d.n_nodes || v >= d.n_nodes) continue;
+        const uint2 mu = d.meta[u];
+        uint32_t ns;
+        if (mu.y != 0u && table_find(d.pool, 4ull * mu.x, table_lg(mu.y), v, ns) != kEmptyId) dup = true;
+        const unsigned long long key = ((unsigned long long)(u < v ? u : v) << 32) | (u < v ? v : u);
+        unsigned long long h = splitmix64(key) & mask;
+        for (unsigned long long probe = 0; probe <= mask; ++probe) {
+            const unsigned long long old = atomicCAS(set + h, ~0ull, key);
+            if (old == ~0ull) break;
+            if (old == key) { dup = true; break; }
+            h = (h + 1u) & mask;
+        }
+    }
+    if (dup) atomicOr(&d.ctrl->status, kStDuplicate);
+}
+
 // Work counters of k_intersect<true>, kept per lane in registers.
 struct Work {
     unsigned long long entries = 0, slots = 0, probes = 0, pslots = 0, wedges = 0, counted = 0;

@@ -17,13 +17,14 @@ from . import _build
 
 REPT_OK = 0
 ERRORS = {-1: "REPT_E_INVAL", -2: "REPT_E_RANGE", -3: "REPT_E_CAPACITY", -4: "REPT_E_NOMEM", -5: "REPT_E_CUDA",
-          -6: "REPT_E_TIMEOUT", -7: "REPT_E_INTERNAL"}
+          -6: "REPT_E_TIMEOUT", -7: "REPT_E_INTERNAL", -8: "REPT_E_SCRATCH", -9: "REPT_E_DUPLICATE"}
 FLAG_FIXED_POOL = 1
 FLAG_SYNC = 2
 FLAG_PROFILE = 4
 FLAG_WORK_COUNTERS = 8
 FLAG_LOCAL_PER_PROCESSOR = 16
 FLAG_MASCOT = 32
+FLAG_CHECK_DUPS = 64
 KERNELS = ("classify", "plan", "commit", "insert", "intersect", "estimate", "sort")
 
 
@@ -90,6 +91,7 @@ def load():
             "rept_destroy": (None, [_vp]),
             "rept_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "rept_kernel_launches": (ctypes.c_uint64, []),
+            "rept_ingest_multi": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -292,3 +294,17 @@ class ReptStream:
         _check(self._lib.rept_kernel_times(self._h, ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(n, ctypes.c_void_p),
                                            int(clear)), "rept_kernel_times")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}
+
+
+def ingest_multi(handles, srcs, dsts, stream=None):
+    """rept_ingest_multi: one batch per handle (srcs[i]/dsts[i] CUDA int32 tensors, possibly empty)
+    through the library's own group for the current device."""
+    lib = load()
+    k = len(handles)
+    hs = (ctypes.c_void_p * k)(*[h.handle.value for h in handles])
+    a = (ctypes.c_void_p * k)(*[x.data_ptr() if x.numel() else None for x in srcs])
+    b = (ctypes.c_void_p * k)(*[x.data_ptr() if x.numel() else None for x in dsts])
+    n = (ctypes.c_uint64 * k)(*[x.numel() for x in srcs])
+    _check(lib.rept_ingest_multi(ctypes.cast(hs, ctypes.c_void_p), ctypes.cast(a, ctypes.c_void_p),
+                                 ctypes.cast(b, ctypes.c_void_p), ctypes.cast(n, ctypes.c_void_p), k,
+                                 _cur_stream(stream)), "rept_ingest_multi")

@@ -68,3 +68,33 @@ def test_batched_small_memory_budget_runs_in_waves():
     for s, (m, c, seed), rb in zip(streams, params, res_b):
         ref = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, seed, pair_counters=False)
         assert np.array_equal(rb.proc, ref.tau_proc) and np.array_equal(rb.local, ref.local1)
+
+
+@pytest.mark.gpu
+def test_ingest_multi_equals_the_oracle():
+    """rept_ingest_multi (the library's own group): several streams fed batch by batch, streams
+    finishing at different rounds (empty batches), more streams than the first call brought (the
+    group is made again, larger), and the oracle's counts for each."""
+    import torch
+    from paper_1811_09136_gb300 import rept
+    streams, params = _mix(k=70, seed=37)
+    dev = [(torch.from_numpy(s.src.view(np.int32)).cuda(), torch.from_numpy(s.dst.view(np.int32)).cuda())
+           for s in streams]
+    handles = [rept.ReptStream(s.n_nodes, m, c, seed, max_batch=1500) for s, (m, c, seed) in zip(streams, params)]
+    try:
+        # first call with 3 streams, then all 70 (more than the 64 the group was sized for)
+        rept.ingest_multi(handles[:3], [d[0][:1500] for d in dev[:3]], [d[1][:1500] for d in dev[:3]])
+        fed = [1500] * 3 + [0] * (len(streams) - 3)
+        while any(f < len(s) for f, s in zip(fed, streams)):
+            a = [d[0][f:f + 1500] for d, f in zip(dev, fed)]
+            b = [d[1][f:f + 1500] for d, f in zip(dev, fed)]
+            rept.ingest_multi(handles, a, b)
+            fed = [min(len(s), f + 1500) for f, s in zip(fed, streams)]
+        for h, s, (m, c, seed) in zip(handles, streams, params):
+            proc, local = h.counts()
+            ref = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, seed, pair_counters=False)
+            assert np.array_equal(proc, ref.tau_proc)
+            assert np.array_equal(local.cpu().numpy().view(np.uint64), ref.local1)
+    finally:
+        for h in handles:
+            h.close()

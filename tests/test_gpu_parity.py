@@ -277,3 +277,36 @@ def test_parallel_mascot_matches_oracle(m, c):
         assert np.array_equal(local.cpu().numpy().view(np.uint64), ref.local1), batch
         assert np.array_equal(lp, ref.tau_local_proc), batch
         assert_estimates_close(g, loc.cpu().numpy(), ref_g, ref_loc)
+
+
+def test_check_dups_flags_repeats_and_leaves_the_state():
+    """REPT_FLAG_CHECK_DUPS: a batch holding an edge twice, or repeating a stored edge of an earlier
+    batch (either orientation), fails with REPT_E_DUPLICATE and is not applied; a clean stream gives
+    the oracle's counts with the check on."""
+    import torch
+    from paper_1811_09136_gb300.rept import ReptStream, ReptError, FLAG_CHECK_DUPS, FLAG_SYNC
+    s = gg.chung_lu(3000, 2.2, 20_000, graph_seed=3, order_seed=4)
+    src, dst = device_edges(s)
+    ref = O.rept_stream(s.src, s.dst, s.n_nodes, 4, 4, 2)
+    with ReptStream(s.n_nodes, 4, 4, 2, max_batch=4096, flags=FLAG_CHECK_DUPS) as r:
+        for off in range(0, len(s), 4096):
+            r.ingest(src[off:off + 4096], dst[off:off + 4096])
+        proc, local = r.counts()
+    assert np.array_equal(proc, ref.tau_proc)
+    assert np.array_equal(local.cpu().numpy().view(np.uint64), ref.local1)
+    half = 10_000
+    for case in ("same_batch", "earlier_batch"):
+        with ReptStream(s.n_nodes, 1, 1, 2, max_batch=4096, flags=FLAG_CHECK_DUPS | FLAG_SYNC) as r:
+            r.ingest(src[:half], dst[:half])
+            before = r.counts()[0].copy()
+            if case == "same_batch":
+                a = torch.cat([src[half:half + 50], src[half + 7:half + 8]])
+                b = torch.cat([dst[half:half + 50], dst[half + 7:half + 8]])
+            else:  # edge 123 again, reversed
+                a = torch.cat([src[half:half + 50], dst[123:124]])
+                b = torch.cat([dst[half:half + 50], src[123:124]])
+            with pytest.raises(ReptError) as ei:
+                r.ingest(a, b)
+            assert ei.value.code == -9, ei.value
+            proc, _, rc = r.counts(allow_error=True)
+            assert rc == -9 and np.array_equal(proc, before), case
