@@ -346,12 +346,22 @@ def run_ours(args, world, rank, local, pg):
         e2e = {"value": world * args.steps * T / el, "unit": "edges/s", "h2d_bytes_per_step": 8 * T,
                "d2h_bytes_per_step": 8 + 8 * s.n_nodes}
 
-    cpu = None
+    cpu = cpu_parallel = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_edges, el = cpu_sample_rate(s, m, c)
         cpu = {"value": n_edges / el, "unit": "edges/s", "cores": 1, "kind": "oracle",
                "sample": f"first {n_edges} edges of the same stream (sequential REPT, {c} processors); "
-                         f"early edges meet smaller sets, so this overstates the oracle's full-stream rate"}
+                         f"early edges meet smaller sets, so this overstates the oracle's full-stream rate",
+               "nproc": os.cpu_count()}
+        # the paper's multi-core design on the same sample: one thread per processor
+        import oracle
+        threads = max(1, min(c, os.cpu_count() or 1))
+        t0 = time.perf_counter()
+        oracle.rept_stream_parallel(s.src[:n_edges], s.dst[:n_edges], s.n_nodes, m, c, SEED, threads)
+        el_p = time.perf_counter() - t0
+        cpu_parallel = {"value": n_edges / el_p, "unit": "edges/s", "threads": threads, "nproc": os.cpu_count(),
+                        "kind": "paper multi-core design (one thread per processor, each with its own pass)",
+                        "sample": f"first {n_edges} edges of the same stream"}
 
     if rank == 0:
         value = world * args.steps * T / (ms_max * 1e-3)
@@ -378,6 +388,7 @@ def run_ours(args, world, rank, local, pg):
                                         "counted", "stored_edges", "class_items", "class_probes",
                                         "class_cycles")},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
+            "cpu_parallel": cpu_parallel,
         }
         print(json.dumps(line), flush=True)
     r.close()

@@ -63,6 +63,9 @@ def load_library(path: str):
     lib.orc_semitriangles.argtypes = [_u32p, _u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint32, ctypes.c_uint64, _u64p, _u64p, _u64p, _u64p,
                                       _u64p, _u64p, _u64p, _u64p]
+    lib.orc_rept_stream_parallel.restype = ctypes.c_int
+    lib.orc_rept_stream_parallel.argtypes = [_u32p, _u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_uint32, ctypes.c_uint64, _u64p, _u64p, _u64p, ctypes.c_int]
     lib.orc_mascot_stream.restype = ctypes.c_int
     lib.orc_mascot_stream.argtypes = [_u32p, _u32p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint32, ctypes.c_uint64, _u64p, _u64p, _u64p, _u64p]
@@ -134,6 +137,21 @@ def rept_stream(src, dst, n: int, m: int, c: int, seed: int, per_proc_local: boo
     if rc != 0:
         raise ValueError(f"orc_rept_stream failed ({rc})")
     return Counts(tau, l1, l2, eta, el, tlp, int(sk[0]))
+
+
+def rept_stream_parallel(src, dst, n: int, m: int, c: int, seed: int, threads: int, lib=None) -> Counts:
+    """tau^(i) and the local sums the paper's multi-core way: one thread per processor, each with its
+    own pass over the stream (no pair counters)."""
+    src, dst = _cols(src, dst)
+    lib = lib or _load()
+    tau = np.zeros(c, dtype=np.uint64)
+    l1 = np.zeros(n, dtype=np.uint64)
+    l2 = np.zeros(n, dtype=np.uint64)
+    rc = lib.orc_rept_stream_parallel(_p(src, _u32p), _p(dst, _u32p), src.size, n, m, c, seed, _p(tau, _u64p),
+                                      _p(l1, _u64p), _p(l2, _u64p), int(threads))
+    if rc != 0:
+        raise ValueError(f"orc_rept_stream_parallel failed ({rc})")
+    return Counts(tau, l1, l2)
 
 
 def estimates(m: int, c: int, counts: Counts, n: int, lib=None):

@@ -22,6 +22,8 @@
  *   orc_mascot_stream,             parallel MASCOT (Section I, III-C): c
  *   orc_mascot_estimates,          independent p = 1/m samplers, sampler i
  *   orc_mascot_semitriangles       keeping h_i colour 0, estimates averaged
+ *   orc_rept_stream_parallel       the same counts the paper's multi-core way:
+ *                                  one thread per processor (a timing baseline)
  *   orc_semitriangles              the definition of a semi-triangle written
  *                                  out as a static triangle enumeration: a
  *                                  triangle counts for processor i iff its two
@@ -160,7 +162,7 @@ static void proc_map(int mascot, uint32_t i, uint32_t m, uint32_t* k, uint32_t* 
 }
 
 static int sample_stream(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32_t n,
-                         uint32_t m, uint32_t c, uint64_t seed, int mascot,
+                         uint32_t m, uint32_t c, uint64_t seed, int mascot, uint32_t i_lo, uint32_t i_hi,
                          uint64_t* tau_proc, uint64_t* eta_proc,
                          uint64_t* local1, uint64_t* local2, uint64_t* eta_local,
                          uint64_t* tau_local_proc, uint64_t* skipped) {
@@ -185,14 +187,14 @@ static int sample_stream(const uint32_t* src, const uint32_t* dst, uint64_t T, u
     vec32 common = {0, 0, 0};
     int rc = 0;
     if (!edges || um_init(&adj_index, 1024)) { free(edges); return -1; }
-    for (uint32_t i = 0; i < c; ++i)
+    for (uint32_t i = i_lo; i < i_hi; ++i)
         if (um_init(&edges[i], 64)) { rc = -1; goto done; }
 
     for (uint64_t t = 0; t < T; ++t) {
         uint32_t u = src[t], v = dst[t];
         if (u >= n || v >= n) { rc = -2; goto done; }
         if (u == v) { if (skipped) ++*skipped; continue; }
-        for (uint32_t i = 0; i < c; ++i) {
+        for (uint32_t i = i_lo; i < i_hi; ++i) {
             uint32_t k, j;
             proc_map(mascot, i, m, &k, &j);
             /* ---- UpdateTriangleCNT(i, (u, v)): N_{u,v}^(i) = N_u^(i) cap N_v^(i) */
@@ -266,7 +268,7 @@ done:
     for (uint64_t q = 0; q < n_lists; ++q) free(lists[q].a);
     free(lists);
     free(common.a);
-    for (uint32_t i = 0; i < c; ++i) um_free(&edges[i]);
+    for (uint32_t i = i_lo; i < i_hi; ++i) um_free(&edges[i]);
     free(edges);
     um_free(&adj_index);
     return rc;
@@ -277,8 +279,50 @@ int orc_rept_stream(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32
                     uint64_t* tau_proc, uint64_t* eta_proc,
                     uint64_t* local1, uint64_t* local2, uint64_t* eta_local,
                     uint64_t* tau_local_proc, uint64_t* skipped) {
-    return sample_stream(src, dst, T, n, m, c, seed, 0, tau_proc, eta_proc, local1, local2, eta_local,
+    return sample_stream(src, dst, T, n, m, c, seed, 0, 0, c, tau_proc, eta_proc, local1, local2, eta_local,
                          tau_local_proc, skipped);
+}
+
+/*
+ * The paper's multi-core design (Section IV): the processors are independent, so each runs
+ * Algorithm 1 over the whole stream with its own sets, one OpenMP thread per processor at a time
+ * (`threads` threads).  Same tau_proc, local1 and local2 as orc_rept_stream; used to time a
+ * multi-core CPU baseline.
+ */
+int orc_rept_stream_parallel(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32_t n,
+                             uint32_t m, uint32_t c, uint64_t seed, uint64_t* tau_proc,
+                             uint64_t* local1, uint64_t* local2, int threads) {
+    if (m == 0 || c == 0 || n == 0 || !tau_proc || !local1 || !local2 || threads < 1) return -1;
+    memset(tau_proc, 0, c * sizeof(uint64_t));
+    memset(local1, 0, (size_t)n * sizeof(uint64_t));
+    memset(local2, 0, (size_t)n * sizeof(uint64_t));
+    int rc = 0;
+    #pragma omp parallel num_threads(threads)
+    {
+        uint64_t* tp = (uint64_t*)calloc(c, sizeof(uint64_t));
+        uint64_t* l1 = (uint64_t*)calloc(n, sizeof(uint64_t));
+        uint64_t* l2 = (uint64_t*)calloc(n, sizeof(uint64_t));
+        uint64_t* a1 = (uint64_t*)calloc(n, sizeof(uint64_t));
+        uint64_t* a2 = (uint64_t*)calloc(n, sizeof(uint64_t));
+        int mine = (tp && l1 && l2 && a1 && a2) ? 0 : -1;
+        #pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < (int64_t)c; ++i) {
+            if (mine) continue;
+            mine = sample_stream(src, dst, T, n, m, c, seed, 0, (uint32_t)i, (uint32_t)i + 1, tp, NULL, l1, l2,
+                                 NULL, NULL, NULL);
+            if (mine) continue;
+            tau_proc[i] = tp[i];
+            for (uint32_t v = 0; v < n; ++v) { a1[v] += l1[v]; a2[v] += l2[v]; }
+        }
+        #pragma omp critical
+        {
+            if (mine) rc = mine;
+            else
+                for (uint32_t v = 0; v < n; ++v) { local1[v] += a1[v]; local2[v] += a2[v]; }
+        }
+        free(tp); free(l1); free(l2); free(a1); free(a2);
+    }
+    return rc;
 }
 
 /*
@@ -290,7 +334,7 @@ int orc_rept_stream(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32
 int orc_mascot_stream(const uint32_t* src, const uint32_t* dst, uint64_t T, uint32_t n,
                       uint32_t m, uint32_t c, uint64_t seed,
                       uint64_t* tau_proc, uint64_t* local1, uint64_t* tau_local_proc, uint64_t* skipped) {
-    return sample_stream(src, dst, T, n, m, c, seed, 1, tau_proc, NULL, local1, NULL, NULL, tau_local_proc,
+    return sample_stream(src, dst, T, n, m, c, seed, 1, 0, c, tau_proc, NULL, local1, NULL, NULL, tau_local_proc,
                          skipped);
 }
 

@@ -26,3 +26,20 @@ def test_generators_contract():
         assert np.unique(key).size == key.size
     a, b = gg.chung_lu(5000, 2.1, 30_000), gg.chung_lu(5000, 2.1, 30_000)
     assert a.sha256() == b.sha256()
+
+
+def test_parallel_design_equals_the_sequential_oracle_and_the_definition():
+    """The one-thread-per-processor oracle (the paper's multi-core design, used as a timing
+    baseline) gives the sequential oracle's counts and the static enumeration's, c <= m, c = c1 m
+    and c mod m != 0, with more and fewer threads than processors."""
+    import numpy as np
+    import oracle as O
+    from paper_1811_09136_gb300 import graphgen as gg
+    s = gg.chung_lu(1500, 2.2, 9000, graph_seed=5, order_seed=6)
+    for (m, c, threads) in [(5, 3, 2), (4, 8, 3), (3, 7, 16)]:
+        a = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, 11, pair_counters=False)
+        b = O.rept_stream_parallel(s.src, s.dst, s.n_nodes, m, c, 11, threads)
+        e = O.semitriangles(s.src, s.dst, s.n_nodes, m, c, 11)
+        assert np.array_equal(a.tau_proc, b.tau_proc) and np.array_equal(b.tau_proc, e.tau_proc)
+        assert np.array_equal(a.local1, b.local1) and np.array_equal(a.local2, b.local2)
+        assert np.array_equal(b.local1, e.local1) and np.array_equal(b.local2, e.local2)
