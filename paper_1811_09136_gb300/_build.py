@@ -24,20 +24,27 @@ def sources() -> list[str]:
                   [os.path.join(INCLUDE, "rept.h")])
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    """Build librept.so if any source is newer than it.  Returns the library path."""
+DEBUG_LIB_PATH = os.path.join(PKG, "librept_debug.so")
+
+
+def build(force: bool = False, verbose_ptxas: bool = False, debug_bounds: bool = False) -> str:
+    """Build librept.so if any source is newer than it.  Returns the library path.  With
+    ``debug_bounds``, build librept_debug.so instead: every pool, queue and node index the kernels use
+    is checked (REPT_DEBUG_BOUNDS), a failed check is recorded and the access skipped, and the next
+    synchronising call reports REPT_E_INTERNAL (a stand-in for a memory checker)."""
+    path = DEBUG_LIB_PATH if debug_bounds else LIB_PATH
     srcs = sources()
-    if not force and os.path.exists(LIB_PATH):
+    if not force and os.path.exists(path):
         newest = max(os.path.getmtime(p) for p in srcs)
-        if os.path.getmtime(LIB_PATH) >= newest:
-            return LIB_PATH
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+        if os.path.getmtime(path) >= newest:
+            return path
+    tmp = path + f".tmp{os.getpid()}"
     cmd = [_nvcc(), *NVCC_FLAGS, "-I", INCLUDE, "-I", CSRC, "-shared", "-o", tmp,
            *sorted(glob.glob(os.path.join(CSRC, "*.cu")))]
     if verbose_ptxas:
         cmd[1:1] = ["-Xptxas", "-v"]
-    if os.environ.get("REPT_DEBUG_BOUNDS"):
+    if debug_bounds:
         cmd[1:1] = ["-DREPT_DEBUG_BOUNDS"]
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, path)
+    return path

@@ -49,6 +49,7 @@ int status_to_code(unsigned st) {
     if (st & kStTimeout) return REPT_E_TIMEOUT;
     if (st & kStInternal) return REPT_E_INTERNAL;
     if (st & kStDuplicate) return REPT_E_DUPLICATE;
+    if (st & kStBounds) return REPT_E_INTERNAL;
     return REPT_OK;
 }
 
@@ -319,6 +320,11 @@ int enqueue_global_estimate(rept_state* s, cudaStream_t st) {
 int sync_status(rept_state* s, cudaStream_t st) {
     int rc = read_ctrl(s, st);
     if (rc) return rc;
+#ifdef REPT_DEBUG_BOUNDS
+    if (s->h_ctrl->dbg[3])
+        std::fprintf(stderr, "rept: index check at site %llu failed: index %llu, bound %llu (%llu failures)\n",
+                     s->h_ctrl->dbg[0], s->h_ctrl->dbg[1], s->h_ctrl->dbg[2], s->h_ctrl->dbg[3]);
+#endif
     return status_to_code(s->h_ctrl->status);
 }
 

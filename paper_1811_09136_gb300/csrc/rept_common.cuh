@@ -43,6 +43,7 @@ constexpr uint16_t kNoKey = 0xFFFFu;
 
 // status bits (sticky)
 constexpr unsigned kStRange = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeout = 8u, kStDuplicate = 16u;
+constexpr unsigned kStBounds = 32u;  // REPT_DEBUG_BOUNDS builds: an index check failed
 
 // x mod m for 64-bit x and 32-bit m >= 2 without a division: Lemire, Kaser, Kurz, "Faster Remainder
 // by Direct Computation" (2019).  With the 128-bit magic M = floor((2^128 - 1) / m) + 1, the low 128
@@ -128,6 +129,7 @@ struct Ctrl {
     unsigned long long n_big;   // nodes whose table (32..2048 slots) k_rehash_big moves, a warp each
     unsigned long long n_huge;  // nodes whose table (>= 4096 slots) k_rehash_huge moves, a block each
     unsigned long long huge_next;
+    unsigned long long dbg[4];  // REPT_DEBUG_BOUNDS builds: first failed check {site, index, bound}, count
 };
 
 // What k_intersect needs about one arriving edge t = (s, l), s the endpoint with the smaller table:
@@ -188,6 +190,25 @@ struct BatchDev {
     unsigned long long n;
     unsigned long long t0;  // stream index of src[0], dst[0]
 };
+
+// Index checks of the REPT_DEBUG_BOUNDS build (a stand-in for a memory checker): a failed check
+// records {site, index, bound} once, counts, raises kStBounds, and the caller skips the access.
+// Release builds compile them away.
+#ifdef REPT_DEBUG_BOUNDS
+__device__ __forceinline__ bool dbg_ok(Ctrl* c, unsigned site, unsigned long long idx, unsigned long long bound) {
+    if (idx < bound) return true;
+    if (atomicAdd(&c->dbg[3], 1ull) == 0ull) {
+        c->dbg[0] = site;
+        c->dbg[1] = idx;
+        c->dbg[2] = bound;
+    }
+    atomicOr(&c->status, kStBounds);
+    return false;
+}
+#define REPT_CHECK(c, site, idx, bound) dbg_ok((c), (site), (idx), (bound))
+#else
+#define REPT_CHECK(c, site, idx, bound) true
+#endif
 
 // One output step of SplitMix64 from state x (Steele, Lea, Flood 2014).
 __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {

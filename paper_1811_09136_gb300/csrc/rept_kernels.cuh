@@ -100,6 +100,12 @@ __device__ __forceinline__ void k_plan_body(const StreamDev& d) {
     }
 }
 
+// REPT_DEBUG_BOUNDS: the block of 2^lg table slots and its list at `off_quads` lies inside the pool.
+__device__ __forceinline__ bool block_fits(const StreamDev& d, unsigned site, unsigned long long off_quads,
+                                          uint32_t lg) {
+    return REPT_CHECK(d.ctrl, site, 4ull * (off_quads + block_quads(lg)) - 1ull, 4ull * d.pool_quads);
+}
+
 // Move node x's entries (list of cnt_old entries at old_off) into its new block at new_off: copy the
 // list (and its colours, when kept) and insert each entry into the new table.  Lanes `rank` of
 // `width` share the work.
@@ -150,7 +156,9 @@ __device__ __forceinline__ void k_commit_body(const StreamDev& d) {
                     huge = !defer;
                 } else {
                     const unsigned long long new_off = top + rel;
-                    if (!move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), 0u, 1u))
+                    const bool fits = block_fits(d, 10, m.x, table_lg(m.y)) &&
+                                      block_fits(d, 11, new_off, table_lg(cnt_new));
+                    if (fits && !move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), 0u, 1u))
                         atomicOr(&d.ctrl->status, kStInternal);
                     d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
                 }
@@ -175,7 +183,8 @@ __device__ __forceinline__ void k_rehash_big_body(const StreamDev& d) {
         const uint2 m = d.meta[x];
         const uint32_t cnt_new = m.y + d.add[x];
         const unsigned long long new_off = top + d.grow_rel[i];
-        if (!move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), lane, 32u))
+        const bool fits = block_fits(d, 10, m.x, table_lg(m.y)) && block_fits(d, 11, new_off, table_lg(cnt_new));
+        if (fits && !move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), lane, 32u))
             atomicOr(&d.ctrl->status, kStInternal);
         __syncwarp();
         if (lane == 0) d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
@@ -200,7 +209,9 @@ __device__ __forceinline__ void k_rehash_huge_body(const StreamDev& d) {
         const uint2 m = d.meta[x];
         const uint32_t cnt_new = m.y + d.add[x];
         const unsigned long long new_off = top + d.grow_rel[i];
-        if (!move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), threadIdx.x, blockDim.x)) s_bad = 1;
+        const bool fits = block_fits(d, 10, m.x, table_lg(m.y)) && block_fits(d, 11, new_off, table_lg(cnt_new));
+        if (fits && !move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), threadIdx.x, blockDim.x))
+            s_bad = 1;
         __syncthreads();
         if (threadIdx.x == 0) {
             if (s_bad) atomicOr(&d.ctrl->status, kStInternal);
@@ -237,7 +248,7 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
         WorkItem it{};
         if (valid && u != v) {
             const uint2 mu = d.meta[u], mv = d.meta[v];
-            if (kept) {
+            if (kept && block_fits(d, 1, mu.x, table_lg(mu.y)) && block_fits(d, 1, mv.x, table_lg(mv.y))) {
                 const uint32_t t = (uint32_t)(b.t0 + e);
                 const uint32_t lu = table_lg(mu.y), lv = table_lg(mv.y);
                 bool ok = table_insert(d.pool, 4ull * mu.x, lu, v, t);
@@ -245,12 +256,14 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
                 if (!ok) atomicOr(&ct->status, kStInternal);
                 // list positions: add[x] counts this batch's entries of x back down to zero
                 const uint32_t pu = mu.y - atomicSub(&d.add[u], 1u), pv = mv.y - atomicSub(&d.add[v], 1u);
-                d.pool[4ull * mu.x + (1ull << lu) + pu] = make_uint2(v, t);
-                d.pool[4ull * mv.x + (1ull << lv) + pv] = make_uint2(u, t);
-                if (d.col) {
-                    const uint8_t j = (uint8_t)colour_of(u, v, d.seed, d.fm);
-                    d.col[4ull * mu.x + (1ull << lu) + pu] = j;
-                    d.col[4ull * mv.x + (1ull << lv) + pv] = j;
+                if (REPT_CHECK(ct, 2, pu, list_slots(lu)) && REPT_CHECK(ct, 2, pv, list_slots(lv))) {
+                    d.pool[4ull * mu.x + (1ull << lu) + pu] = make_uint2(v, t);
+                    d.pool[4ull * mv.x + (1ull << lv) + pv] = make_uint2(u, t);
+                    if (d.col) {
+                        const uint8_t j = (uint8_t)colour_of(u, v, d.seed, d.fm);
+                        d.col[4ull * mu.x + (1ull << lu) + pu] = j;
+                        d.col[4ull * mv.x + (1ull << lv) + pv] = j;
+                    }
                 }
                 if (d.edge_ends) d.edge_ends[t] = make_uint2(u, v);
             }
@@ -418,6 +431,7 @@ __device__ __forceinline__ void pair_event(const StreamDev& d, uint32_t t, uint3
 
 __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, uint32_t l, uint32_t w,
                                                 unsigned long long* s_proc) {
+    if (!REPT_CHECK(d.ctrl, 9, max(w, max(s, l)), d.n_nodes)) return 0u;
     uint32_t found = 0, found2 = 0;
     uint32_t t_sw = kEmptyId, t_lw = kEmptyId;
     for (uint32_t k = 0; k < d.groups; ++k) {
@@ -486,6 +500,7 @@ __device__ __forceinline__ void mq_push(const StreamDev& d, MatchQueue& q, bool 
                                         uint32_t w, unsigned long long* s_proc, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned mask = __ballot_sync(0xFFFFFFFFu, has);
+    if (!REPT_CHECK(d.ctrl, 13, q.n + __popc(mask), (unsigned long long)kMatchQ + 1ull)) return;
     if (has) {
         const uint32_t i = q.n + __popc(mask & ((1u << lane) - 1u));
         q.s[i] = s;
@@ -508,7 +523,8 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
     uint32_t w = 0;
     if (valid && j < x.cnt_s) {
         const unsigned long long at = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu)) + j;
-        const uint2 es = d.pool[at];
+        const bool fits = REPT_CHECK(d.ctrl, 3, at, 4ull * d.pool_quads) && block_fits(d, 4, x.off_l, x.lgs >> 8);
+        const uint2 es = fits ? d.pool[at] : make_uint2(kEmptyId, kEmptyId);
         if (WORK && j == 0) { wk.entries += x.cnt_s; wk.slots += x.cnt_s; }
         if (es.y < x.t && (!d.col || wedge_may_count(d, x.l, es.x, d.col[at]))) {
             uint32_t nslots = 0;
@@ -552,6 +568,9 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
     const uint32_t lg_l = x.lgs >> 8, n_s = x.cnt_s;
     const unsigned long long base_l = 4ull * x.off_l;
     if (WORK && lane == 0) { wk.entries += n_s; wk.slots += n_s; }
+    if (!(block_fits(d, 5, x.off_s, x.lgs & 0xFFu) && REPT_CHECK(d.ctrl, 6, n_s, list_slots(x.lgs & 0xFFu) + 1u) &&
+          block_fits(d, 7, x.off_l, lg_l)))
+        return;  // (uniform over the warp: x is)
     // the smaller endpoint's entry list (32-byte aligned), read 128 entries per pass, two per 16-byte
     // load; their colours (when kept) two per 2-byte load
     const unsigned long long at_s = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu));
@@ -579,6 +598,7 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
     if (COLOURED) load_pass(0u);
     uint32_t n_q = 0;
     for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
+        if (!REPT_CHECK(d.ctrl, 8, n_q, kRound)) break;
         if (!COLOURED) load_pass(j0);
         const uint4 cq[2] = {nq[0], nq[1]};
         const uint32_t cc[2] = {nc[0], nc[1]};
@@ -913,7 +933,9 @@ __device__ __forceinline__ void group_drain_tiles(const StreamDev* __restrict__ 
                 x = group_item(d, cls, i - pc[sid]);
                 if (j < x.cnt_s) {
                     const unsigned long long at = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu)) + j;
-                    const uint2 es = d.pool[at];
+                    const bool fits = REPT_CHECK(d.ctrl, 3, at, 4ull * d.pool_quads) &&
+                                      block_fits(d, 4, x.off_l, x.lgs >> 8);
+                    const uint2 es = fits ? d.pool[at] : make_uint2(kEmptyId, kEmptyId);
                     if (es.y < x.t && (!d.col || wedge_may_count(d, x.l, es.x, d.col[at]))) {
                         uint32_t nslots = 0;
                         has = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, es.x, nslots) < x.t;

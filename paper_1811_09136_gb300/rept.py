@@ -56,7 +56,9 @@ _u64 = ctypes.c_uint64
 
 
 def library_path() -> str:
-    return _build.LIB_PATH
+    """The in-tree librept.so, or the library named by REPT_LIBRARY (e.g. the bounds-checked debug
+    build, paper_1811_09136_gb300/librept_debug.so)."""
+    return os.environ.get("REPT_LIBRARY") or _build.LIB_PATH
 
 
 def load():
