@@ -1,6 +1,7 @@
 """The CPU oracle against facts fixed by the paper and by mathematics (no GPU)."""
 import pytest
 
+import oracle as O
 import oracle_pins as P
 from paper_1811_09136_gb300 import graphgen as gg
 
@@ -43,3 +44,19 @@ def test_parallel_design_equals_the_sequential_oracle_and_the_definition():
         assert np.array_equal(a.tau_proc, b.tau_proc) and np.array_equal(b.tau_proc, e.tau_proc)
         assert np.array_equal(a.local1, b.local1) and np.array_equal(a.local2, b.local2)
         assert np.array_equal(b.local1, e.local1) and np.array_equal(b.local2, e.local2)
+
+
+def test_oracle_clean_under_address_and_undefined_behaviour_sanitizers(tmp_path):
+    """Every oracle routine on random small graphs, built with -fsanitize=address,undefined (abort
+    on the first report): no memory error, no undefined behaviour, and the routines agree."""
+    import os
+    import subprocess
+    here = os.path.dirname(os.path.abspath(__file__))
+    exe = str(tmp_path / "oracle_sanitize")
+    subprocess.check_call(["gcc", "-O1", "-g", "-std=gnu11", "-fopenmp", "-fsanitize=address,undefined",
+                           "-fno-sanitize-recover=all", "-fno-omit-frame-pointer",
+                           os.path.join(here, "native", "oracle_sanitize.c"), O._SRC, "-o", exe])
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=0", UBSAN_OPTIONS="print_stacktrace=1")
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=300, env=env)
+    assert out.returncode == 0, out.stdout + out.stderr[-4000:]
+    assert "oracle sanitize failures: 0" in out.stdout
