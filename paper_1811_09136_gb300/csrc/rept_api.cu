@@ -1,6 +1,7 @@
 // C ABI of the REPT streaming counter (declared in include/rept.h): handle
 // lifetime, pool sizing, batch launch sequence, estimates.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -165,9 +166,22 @@ cudaEvent_t take_event(rept_state* s) {
     return e;
 }
 
-// Launch `fn` on `st`; with REPT_FLAG_PROFILE bracket it with events on the same stream.
+// NVTX range names of the phases (seen by profilers that record NVTX, e.g. ncu --nvtx); the
+// ranges cost a check of a function pointer when no tool is attached.
+const char* const kPhaseNames[] = {"rept classify", "rept plan", "rept commit", "rept insert",
+                                   "rept intersect", "rept estimate", "rept sort"};
+static_assert(sizeof(kPhaseNames) / sizeof(kPhaseNames[0]) == REPT_NUM_KERNELS, "a name per phase");
+
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+// Launch `fn` on `st` inside an NVTX range named for the phase; with REPT_FLAG_PROFILE bracket it
+// with events on the same stream.
 template <class F>
 int timed_launch(rept_state* s, int kernel, cudaStream_t st, F&& fn, int kernels_in_fn = 1) {
+    NvtxRange range(kPhaseNames[kernel]);
     const bool prof = (s->cfg.flags & REPT_FLAG_PROFILE) != 0;
     cudaEvent_t a = nullptr, b = nullptr;
     if (prof) {
@@ -952,6 +966,7 @@ void rept_group_destroy(rept_group* g) {
 int rept_group_ingest(rept_group* g, rept_state* const* hs, const uint32_t* const* d_src,
                       const uint32_t* const* d_dst, const uint64_t* n, uint32_t k, void* stream) {
     if (!g || !hs || !d_src || !d_dst || !n || k == 0 || k > g->max_streams) return REPT_E_INVAL;
+    NvtxRange range("rept group ingest");
     cudaStream_t st = as_stream(stream);
     unsigned long long max_n = 0;
     uint32_t max_c = 1;
