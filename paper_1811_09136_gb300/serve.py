@@ -32,7 +32,9 @@ class Request:
     c: int
     seed: int
     chunk: int = 1 << 18      # edges fed per round
+    cancel_after: float = math.inf  # the client gives up this many seconds after arrival
     # filled in by the server
+    cancelled: bool = False
     admitted: float = math.nan
     done: float = math.nan
     tau_hat: float = math.nan
@@ -51,12 +53,13 @@ class _Live:
     ready: object = None       # CUDA event: edges uploaded
     waited: bool = False       # the compute stream already waits for the upload
     out: tuple = ()            # pinned result buffers (tau_hat, tau^(i), status)
-    done_ev: object = None     # CUDA event: results copied to the host
+    done_ev: object = None     # CUDA event: results copied to the host (or, if cancelled, its rounds done)
 
 
 @dataclass
 class ServeReport:
     requests: list = field(default_factory=list)
+    cancelled: list = field(default_factory=list)
     makespan: float = 0.0
     edges: int = 0
     rounds: int = 0
@@ -67,7 +70,8 @@ class ServeReport:
 
     def summary(self) -> dict:
         lat = self.latencies()
-        return {"requests": len(self.requests), "edges": self.edges, "makespan_s": self.makespan,
+        return {"requests": len(self.requests), "cancelled": len(self.cancelled), "edges": self.edges,
+                "makespan_s": self.makespan,
                 "edges_per_s": self.edges / self.makespan if self.makespan > 0 else 0.0,
                 "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                 "mean_latency_s": float(lat.mean()), "rounds": self.rounds, "max_live": self.max_live}
@@ -89,7 +93,12 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
     memory, completion seen through a CUDA event), so the next round starts at once.  Finished
     handles are kept and reused (rept_reset_async) by later streams of the same shape; they are
     destroyed only when admission needs their memory, because releasing device memory waits for
-    the whole device."""
+    the whole device.
+
+    A request whose client gives up (``cancel_after`` seconds after its arrival) before its last
+    chunk was fed is cancelled: dropped if it is still waiting, otherwise no longer fed, and its
+    handle becomes a spare once its rounds already on the GPU have finished.  Cancelled requests
+    are listed in ``report.cancelled`` with no estimates; the others are unaffected."""
     import torch
 
     torch.cuda.synchronize()
@@ -140,9 +149,23 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
     t0 = clock()
     while pending or live or completing:
         now = clock() - t0
+        # cancellations: live requests stop being fed; their rounds in flight finish first
+        for x in [x for x in live if now >= x.req.arrival + x.req.cancel_after]:
+            x.req.cancelled = True
+            x.done_ev = torch.cuda.Event()
+            x.done_ev.record(compute)
+            x.src = x.dst = None
+            live.remove(x)
+            completing.append(x)
         # results whose copies have landed
         for x in [x for x in completing if x.done_ev.query()]:
             r = x.req
+            if r.cancelled:
+                r.done = clock() - t0
+                rep.cancelled.append(r)
+                completing.remove(x)
+                graveyard.append(x)
+                continue
             g, proc, status = x.out
             if int(status[0]) != 0:
                 x.handle.sync()  # raises the handle's REPT_E_* error
@@ -161,6 +184,12 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
         # admission: arrived, a slot free, state fits the remaining budget (FIFO, no overtaking)
         while pending and pending[-1].arrival <= now and len(live) < max_live:
             r = pending[-1]
+            if now >= r.arrival + r.cancel_after:  # given up before it was admitted
+                pending.pop()
+                r.cancelled = True
+                r.done = now
+                rep.cancelled.append(r)
+                continue
             need = batched._state_bytes(r.stream.n_nodes, len(r.stream), feed(r)) + 8 * len(r.stream)
             reuse = spare.get(shape(r))
             if reuse:
@@ -233,6 +262,7 @@ def serve(requests: list[Request], max_live: int = 256, budget_bytes: int | None
     destroy_spares()
     group.close()
     rep.requests.sort(key=lambda r: r.rid)
+    rep.cancelled.sort(key=lambda r: r.rid)
     return rep
 
 

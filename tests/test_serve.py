@@ -57,3 +57,35 @@ def test_reused_handles_give_the_same_results():
         g, proc, local = serve.count_alone(r)
         assert np.array_equal(r.proc, proc) and np.array_equal(r.local, local)
         assert abs(r.tau_hat - g) <= 1e-12 * max(abs(g), 1.0)
+
+
+@pytest.mark.gpu
+def test_cancelled_requests_leave_the_others_exact():
+    """A request given up before admission is dropped; one given up after admission stops being fed
+    (its rounds in flight finish) and its handle is reused; every other request still gets exactly
+    its counts alone.  A fake clock (1 ms per reading) makes the timing deterministic."""
+    reqs = _trace(n=10, rate=400.0)
+    longest = max(range(1, 10), key=lambda i: len(reqs[i].stream))
+    reqs[longest].chunk = 1 << 8
+    reqs[longest].cancel_after = 0.01          # about ten clock readings after its arrival
+    reqs[0].cancel_after = 0.0                 # gives up at once, before admission
+
+    class Tick:
+        t = 0.0
+
+        def __call__(self):
+            self.t += 0.001
+            return self.t
+
+    rep = serve.serve(reqs, max_live=8, keep_local=True, clock=Tick())
+    cancelled = {r.rid for r in rep.cancelled}
+    assert cancelled == {0, longest}, cancelled
+    gone = {r.rid: r for r in rep.cancelled}
+    assert np.isnan(gone[0].admitted) and not np.isnan(gone[longest].admitted)
+    assert all(np.isnan(r.tau_hat) for r in rep.cancelled)
+    assert len(rep.requests) == len(reqs) - 2
+    for r in rep.requests:
+        g, proc, local = serve.count_alone(r)
+        assert np.array_equal(r.proc, proc) and np.array_equal(r.local, local)
+        assert abs(r.tau_hat - g) <= 1e-12 * max(abs(g), 1.0)
+    assert rep.summary()["cancelled"] == 2
