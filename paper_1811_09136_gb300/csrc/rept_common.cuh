@@ -106,7 +106,13 @@ __host__ __device__ __forceinline__ bool mod_equals(uint64_t x, uint32_t j, cons
     if (f.m < 2) return j == 0u;
     if (j >= f.m || x < j) return false;
     const uint64_t y = (x - j) * f.qinv;
+#ifdef __CUDA_ARCH__
+    // rotate right by k < 32 (m < 2^32): each half is a funnel shift of the two halves
+    const uint32_t lo = (uint32_t)y, hi = (uint32_t)(y >> 32);
+    const uint64_t r = ((uint64_t)__funnelshift_r(hi, lo, f.k) << 32) | __funnelshift_r(lo, hi, f.k);
+#else
     const uint64_t r = (y >> f.k) | (y << ((64u - f.k) & 63u));
+#endif
     return r <= f.lim;
 }
 
