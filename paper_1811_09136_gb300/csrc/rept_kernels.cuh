@@ -171,10 +171,58 @@ __device__ __forceinline__ void k_commit_body(const StreamDev& d) {
     }
 }
 
+// Tables of at most kMoveSlots slots are rebuilt in shared memory when a warp moves a block.
+constexpr uint32_t kMoveSlots = 512;
+
+// move_block for one warp, the new table built in shared memory (keys and stream indices of
+// 2^lg_new <= kMoveSlots slots, the same placement rule as table_insert) and then written out with
+// coalesced stores.  The new block is this warp's alone until the batch's inserts run.
+__device__ __forceinline__ bool move_block_smem(uint2* pool, uint8_t* col, uint32_t old_off, uint32_t cnt_old,
+                                                unsigned long long new_off, uint32_t lg_new, uint32_t* s_keys,
+                                                uint32_t* s_eidx, unsigned lane) {
+    const uint32_t cap = 1u << lg_new, mask = cap - 1u;
+    for (uint32_t q = lane; q < cap; q += 32u) {
+        s_keys[q] = kEmptyId;
+        s_eidx[q] = kEmptyId;
+    }
+    __syncwarp();
+    const unsigned long long old_at = 4ull * old_off + (1ull << table_lg(cnt_old));
+    const unsigned long long new_at = 4ull * new_off + cap;
+    bool ok = true;
+    for (uint32_t j = lane; j < cnt_old; j += 32u) {
+        const uint2 e = pool[old_at + j];
+        pool[new_at + j] = e;
+        if (col) col[new_at + j] = col[old_at + j];
+        const uint32_t start = (e.x * 0x85EBCA6Bu) >> 30;
+        uint32_t b = home_slot(e.x, lg_new);
+        bool placed = false;
+        for (uint32_t probe = 0; probe <= mask && !placed; probe += 4u) {
+            for (uint32_t i = 0; i < 4u && !placed; ++i) {
+                const uint32_t h = b + ((start + i) & 3u);
+                if (atomicCAS(&s_keys[h], kEmptyId, e.x) == kEmptyId) {
+                    s_eidx[h] = e.y;
+                    placed = true;
+                }
+            }
+            b = (b + 4u) & mask;
+        }
+        ok &= placed;
+    }
+    __syncwarp();
+    uint32_t* keys = reinterpret_cast<uint32_t*>(pool + 4ull * new_off);
+    for (uint32_t q = lane; q < cap; q += 32u) {
+        keys[q] = s_keys[q];
+        keys[cap + q] = s_eidx[q];
+    }
+    return ok;
+}
+
 // Move the blocks of 9..2048 entries listed by k_commit: one warp per node.
 __device__ __forceinline__ void k_rehash_big_body(const StreamDev& d) {
+    __shared__ uint32_t s_keys[8][kMoveSlots];  // blocks of 256 threads
+    __shared__ uint32_t s_eidx[8][kMoveSlots];
     const unsigned long long n_big = d.ctrl->n_big, top = d.ctrl->pool_top;
-    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     for (unsigned long long k = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_big;
          k += warps) {
@@ -184,8 +232,13 @@ __device__ __forceinline__ void k_rehash_big_body(const StreamDev& d) {
         const uint32_t cnt_new = m.y + d.add[x];
         const unsigned long long new_off = top + d.grow_rel[i];
         const bool fits = block_fits(d, 10, m.x, table_lg(m.y)) && block_fits(d, 11, new_off, table_lg(cnt_new));
-        if (fits && !move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), lane, 32u))
-            atomicOr(&d.ctrl->status, kStInternal);
+        const uint32_t lg_new = table_lg(cnt_new);
+        bool ok = true;
+        if (fits && (1u << lg_new) <= kMoveSlots && REPT_CHECK(d.ctrl, 14, wid, 8u))
+            ok = move_block_smem(d.pool, d.col, m.x, m.y, new_off, lg_new, s_keys[wid], s_eidx[wid], lane);
+        else if (fits)
+            ok = move_block(d.pool, d.col, m.x, m.y, new_off, lg_new, lane, 32u);
+        if (!ok) atomicOr(&d.ctrl->status, kStInternal);
         __syncwarp();
         if (lane == 0) d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
     }
@@ -1095,9 +1148,10 @@ __global__ void k_commit_multi(const StreamDev* __restrict__ ds, const BatchDev*
     k_commit_body(sd);
 }
 
-__global__ void k_rehash_big(StreamDev d) { k_rehash_big_body(d); }
+__global__ void __launch_bounds__(256) k_rehash_big(StreamDev d) { k_rehash_big_body(d); }
 
-__global__ void k_rehash_big_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
+__global__ void __launch_bounds__(256) k_rehash_big_multi(const StreamDev* __restrict__ ds,
+                                                            const BatchDev* __restrict__ bs) {
     (void)bs;
     __shared__ StreamDev sd;
     if (threadIdx.x == 0) sd = ds[blockIdx.y];
