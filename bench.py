@@ -200,7 +200,7 @@ def cpu_sample_rate(s, m, c, budget_s=15.0):
 # DRAM bytes (read + write) per k_intersect launch, the mean over the 15 launches of one step from an
 # ncu capture of the current kernel (profiles/k_intersect_rmat_s20_c100.md); absent for workloads not
 # captured.  Must be removed when the kernel changes.
-K3_TRAFFIC = {("rmat_s20", 100): 981.0e6}
+K3_TRAFFIC = {}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -302,9 +302,8 @@ def run_ours(args, world, rank, local, pg):
         proc_w, _ = rw.counts()
         st = rw.stats()
     assert np.array_equal(proc_w, proc), "work-counter pass disagrees with the timed pass"
-    # per list entry scanned: 8 B {neighbour, stream index}, plus its 1-byte colour when the library
-    # keeps colours beside the lists (one hash group, 2 <= m <= 256)
-    per_entry = 8 + (1 if c <= m and 2 <= m <= 256 else 0)
+    # per list entry scanned: 8 B {neighbour (with its colour in the top bits), stream index}
+    per_entry = 8
     k3_bytes = 24 * (T - st["self_loops"]) + per_entry * st["small_entries"] + 8 * st["probes"] + 16 * st["counted"]
     # bytes a step touches: its edges, the node blocks it fills (8-byte slots plus colour bytes) and
     # the per-node arrays (meta, local, add)

@@ -113,16 +113,9 @@ int grow_pool(rept_state* s, unsigned long long min_quads, cudaStream_t st) {
     const unsigned long long used = s->h_ctrl->pool_top;
     if (s->d.pool && used) REPT_CUDA(cudaMemcpyAsync(np, s->d.pool, used * 32ull, cudaMemcpyDeviceToDevice, st));
     REPT_CUDA(cudaMemsetAsync((char*)np + used * 32ull, 0xFF, (want - used) * 32ull, st));
-    uint8_t* nc = nullptr;
-    if (s->d.col) {
-        if ((rc = dev_alloc(s, (void**)&nc, want * 4ull))) return rc;
-        if (used) REPT_CUDA(cudaMemcpyAsync(nc, s->d.col, used * 4ull, cudaMemcpyDeviceToDevice, st));
-    }
     REPT_CUDA(cudaStreamSynchronize(st));
     dev_free(s, s->d.pool, s->d.pool_quads * 32ull);
-    if (s->d.col) dev_free(s, s->d.col, s->d.pool_quads * 4ull);
     s->d.pool = np;
-    s->d.col = nc;
     s->d.pool_quads = want;
     return REPT_OK;
 }
@@ -296,7 +289,7 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
     const size_t smem = s->cfg.c * sizeof(unsigned long long);
     const bool work = (s->cfg.flags & REPT_FLAG_WORK_COUNTERS) != 0;
     rc = timed_launch(s, REPT_K_INTERSECT, st, [&] {
-        if (s->d.col) {
+        if (s->d.colours) {
             if (work) k_intersect<true><<<grid_i, 256, smem, st>>>(s->d, b);
             else k_intersect<false><<<grid_i, 256, smem, st>>>(s->d, b);
         } else {
@@ -370,7 +363,8 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
         return fail(REPT_E_CUDA);
     // the intersection grid: as many blocks as fit at once, for the variant this stream uses
     const bool coloured = (cfg->flags & REPT_FLAG_MASCOT ? cfg->c : (cfg->c + cfg->m - 1) / cfg->m) == 1 &&
-                          cfg->m >= 2 && cfg->m <= 256;
+                          cfg->m >= 2 && cfg->m <= 256 &&
+                          cfg->n_nodes <= (1u << kIdBits);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coloured ? (const void*)k_intersect<false>
                                                                         : (const void*)k_intersect_probe<false>,
@@ -401,10 +395,8 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if ((rc = dev_alloc(s, (void**)&d.pool, quads * 32ull))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&s->d_global, sizeof(double)))) return fail(rc);
     d.pool_quads = quads;
-    // one hash group with few colours: keep each list entry's colour beside it (one byte per slot)
-    if (coloured) {
-        if ((rc = dev_alloc(s, (void**)&d.col, quads * 4ull))) return fail(rc);
-    }
+    // one hash group, few colours and ids of at most kIdBits: list entries carry their colour
+    d.colours = coloured ? 1u : 0u;
     d.c1 = mascot || cfg->c <= cfg->m ? cfg->c : cfg->c / cfg->m;
     d.keep = mascot ? 1u : cfg->m;
     d.pstride = mascot ? 1u : cfg->m;
@@ -632,7 +624,6 @@ int snap_parts(rept_state* s, unsigned long long pool_top, SnapPart* parts, int*
     parts[k++] = {d.local, n * 8ull};
     parts[k++] = {d.proc, c * 8ull};
     parts[k++] = {d.pool, pool_top * 32ull};
-    if (d.col) parts[k++] = {d.col, pool_top * 4ull};
     if (d.local2) {
         parts[k++] = {d.local2, n * 8ull};
         parts[k++] = {d.eta_proc, c * 8ull};
@@ -795,7 +786,6 @@ void rept_destroy(rept_state* s) {
     cudaFree(d.add);
     cudaFree(d.ctrl);
     cudaFree(d.pool);
-    cudaFree(d.col);
     cudaFree(d.touched);
     cudaFree(d.grow_rel);
     cudaFree(d.big);

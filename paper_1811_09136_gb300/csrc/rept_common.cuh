@@ -30,6 +30,8 @@ namespace rept {
 constexpr uint32_t kEmptyId = 0xFFFFFFFFu;
 constexpr unsigned long long kEmptySlot = 0xFFFFFFFFFFFFFFFFull;
 constexpr uint64_t kGoldenGamma = 0x9E3779B97F4A7C15ull;  // SplitMix64 increment
+constexpr uint32_t kIdBits = 24;                             // node-id bits of a list entry with a colour
+constexpr uint32_t kIdMask = (1u << kIdBits) - 1u;
 constexpr uint32_t kNoGrow = 0xFFFFFFFFu;
 constexpr uint32_t kMaxProcessors = 4096;  // per-block tau^(i) histogram lives in shared memory
 // Number of k_intersect work classes (see bin_of_cnt).
@@ -158,9 +160,10 @@ struct StreamDev {
     uint2* meta;
     uint2* pool;
     unsigned long long pool_quads;
-    // [4 * pool_quads] one byte per pool slot: for a list entry {w, t} of node x in that slot, the
-    // colour h_0(x, w).  Kept for one hash group with m <= 256 colours, else NULL.
-    uint8_t* col;
+    // 1: every list entry {w, t} of node x carries the colour h_0(x, w) in the top 8 bits of its
+    // first word (w itself in the low kIdBits), kept for one hash group, 2 <= m <= 256 and
+    // n_nodes <= 2^kIdBits; 0: list entries hold plain ids
+    uint32_t colours;
     unsigned long long* local;
     unsigned long long* proc;
     uint32_t* add;
@@ -254,10 +257,13 @@ __device__ __forceinline__ bool kept_by_any(const StreamDev& d, uint32_t u, uint
     return false;
 }
 
+// The mask that takes a node id out of the first word of a list entry.
+__host__ __device__ __forceinline__ uint32_t id_mask(const StreamDev& d) { return d.colours ? kIdMask : ~0u; }
+
 // With one hash group, a wedge (s, w), (l, w) can count only for the processor of colour
 // js = h_0(s, w), and only if that processor exists and h_0(l, w) = js.  The intersection reads js from
-// the colour array next to s's list and asks this of the hash alone before it probes l's table for w,
-// so all but about 1/m of the probes are skipped.
+// s's list entry and asks this of the hash alone before it probes l's table for w, so all but about
+// 1/m of the probes are skipped.
 __device__ __forceinline__ bool wedge_may_count(const StreamDev& d, uint32_t l, uint32_t w, uint32_t js) {
     uint32_t i;
     return processor_of(d, 0u, js, i) && colour_is(l, w, d.seed, d.fm, js);

@@ -107,9 +107,9 @@ __device__ __forceinline__ bool block_fits(const StreamDev& d, unsigned site, un
 }
 
 // Move node x's entries (list of cnt_old entries at old_off) into its new block at new_off: copy the
-// list (and its colours, when kept) and insert each entry into the new table.  Lanes `rank` of
-// `width` share the work.
-__device__ __forceinline__ bool move_block(uint2* pool, uint8_t* col, uint32_t old_off, uint32_t cnt_old,
+// list and insert each entry's id (`mask` takes it out of the entry) into the new table.  Lanes
+// `rank` of `width` share the work.
+__device__ __forceinline__ bool move_block(uint2* pool, uint32_t mask, uint32_t old_off, uint32_t cnt_old,
                                            unsigned long long new_off, uint32_t lg_new, uint32_t rank, uint32_t width) {
     const unsigned long long old_at = 4ull * old_off + (1ull << table_lg(cnt_old));
     const unsigned long long new_at = 4ull * new_off + (1ull << lg_new);
@@ -119,8 +119,7 @@ __device__ __forceinline__ bool move_block(uint2* pool, uint8_t* col, uint32_t o
     for (uint32_t j = rank; j < cnt_old; j += width) {
         const uint2 e = old_list[j];
         new_list[j] = e;
-        if (col) col[new_at + j] = col[old_at + j];
-        ok &= table_insert(pool, 4ull * new_off, lg_new, e.x, e.y);
+        ok &= table_insert(pool, 4ull * new_off, lg_new, e.x & mask, e.y);
     }
     return ok;
 }
@@ -158,7 +157,7 @@ __device__ __forceinline__ void k_commit_body(const StreamDev& d) {
                     const unsigned long long new_off = top + rel;
                     const bool fits = block_fits(d, 10, m.x, table_lg(m.y)) &&
                                       block_fits(d, 11, new_off, table_lg(cnt_new));
-                    if (fits && !move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), 0u, 1u))
+                    if (fits && !move_block(d.pool, id_mask(d), m.x, m.y, new_off, table_lg(cnt_new), 0u, 1u))
                         atomicOr(&d.ctrl->status, kStInternal);
                     d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
                 }
@@ -177,7 +176,7 @@ constexpr uint32_t kMoveSlots = 512;
 // move_block for one warp, the new table built in shared memory (keys and stream indices of
 // 2^lg_new <= kMoveSlots slots, the same placement rule as table_insert) and then written out with
 // coalesced stores.  The new block is this warp's alone until the batch's inserts run.
-__device__ __forceinline__ bool move_block_smem(uint2* pool, uint8_t* col, uint32_t old_off, uint32_t cnt_old,
+__device__ __forceinline__ bool move_block_smem(uint2* pool, uint32_t id_bits, uint32_t old_off, uint32_t cnt_old,
                                                 unsigned long long new_off, uint32_t lg_new, uint32_t* s_keys,
                                                 uint32_t* s_eidx, unsigned lane) {
     const uint32_t cap = 1u << lg_new, mask = cap - 1u;
@@ -192,14 +191,14 @@ __device__ __forceinline__ bool move_block_smem(uint2* pool, uint8_t* col, uint3
     for (uint32_t j = lane; j < cnt_old; j += 32u) {
         const uint2 e = pool[old_at + j];
         pool[new_at + j] = e;
-        if (col) col[new_at + j] = col[old_at + j];
-        const uint32_t start = (e.x * 0x85EBCA6Bu) >> 30;
-        uint32_t b = home_slot(e.x, lg_new);
+        const uint32_t key = e.x & id_bits;
+        const uint32_t start = (key * 0x85EBCA6Bu) >> 30;
+        uint32_t b = home_slot(key, lg_new);
         bool placed = false;
         for (uint32_t probe = 0; probe <= mask && !placed; probe += 4u) {
             for (uint32_t i = 0; i < 4u && !placed; ++i) {
                 const uint32_t h = b + ((start + i) & 3u);
-                if (atomicCAS(&s_keys[h], kEmptyId, e.x) == kEmptyId) {
+                if (atomicCAS(&s_keys[h], kEmptyId, key) == kEmptyId) {
                     s_eidx[h] = e.y;
                     placed = true;
                 }
@@ -235,9 +234,9 @@ __device__ __forceinline__ void k_rehash_big_body(const StreamDev& d) {
         const uint32_t lg_new = table_lg(cnt_new);
         bool ok = true;
         if (fits && (1u << lg_new) <= kMoveSlots && REPT_CHECK(d.ctrl, 14, wid, 8u))
-            ok = move_block_smem(d.pool, d.col, m.x, m.y, new_off, lg_new, s_keys[wid], s_eidx[wid], lane);
+            ok = move_block_smem(d.pool, id_mask(d), m.x, m.y, new_off, lg_new, s_keys[wid], s_eidx[wid], lane);
         else if (fits)
-            ok = move_block(d.pool, d.col, m.x, m.y, new_off, lg_new, lane, 32u);
+            ok = move_block(d.pool, id_mask(d), m.x, m.y, new_off, lg_new, lane, 32u);
         if (!ok) atomicOr(&d.ctrl->status, kStInternal);
         __syncwarp();
         if (lane == 0) d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
@@ -263,7 +262,7 @@ __device__ __forceinline__ void k_rehash_huge_body(const StreamDev& d) {
         const uint32_t cnt_new = m.y + d.add[x];
         const unsigned long long new_off = top + d.grow_rel[i];
         const bool fits = block_fits(d, 10, m.x, table_lg(m.y)) && block_fits(d, 11, new_off, table_lg(cnt_new));
-        if (fits && !move_block(d.pool, d.col, m.x, m.y, new_off, table_lg(cnt_new), threadIdx.x, blockDim.x))
+        if (fits && !move_block(d.pool, id_mask(d), m.x, m.y, new_off, table_lg(cnt_new), threadIdx.x, blockDim.x))
             s_bad = 1;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -310,13 +309,10 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
                 // list positions: add[x] counts this batch's entries of x back down to zero
                 const uint32_t pu = mu.y - atomicSub(&d.add[u], 1u), pv = mv.y - atomicSub(&d.add[v], 1u);
                 if (REPT_CHECK(ct, 2, pu, list_slots(lu)) && REPT_CHECK(ct, 2, pv, list_slots(lv))) {
-                    d.pool[4ull * mu.x + (1ull << lu) + pu] = make_uint2(v, t);
-                    d.pool[4ull * mv.x + (1ull << lv) + pv] = make_uint2(u, t);
-                    if (d.col) {
-                        const uint8_t j = (uint8_t)colour_of(u, v, d.seed, d.fm);
-                        d.col[4ull * mu.x + (1ull << lu) + pu] = j;
-                        d.col[4ull * mv.x + (1ull << lv) + pv] = j;
-                    }
+                    // with colours, h_0(u, v) rides in the top bits of both entries
+                    const uint32_t cj = d.colours ? colour_of(u, v, d.seed, d.fm) << kIdBits : 0u;
+                    d.pool[4ull * mu.x + (1ull << lu) + pu] = make_uint2(v | cj, t);
+                    d.pool[4ull * mv.x + (1ull << lv) + pv] = make_uint2(u | cj, t);
                 }
                 if (d.edge_ends) d.edge_ends[t] = make_uint2(u, v);
             }
@@ -579,12 +575,13 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
         const bool fits = REPT_CHECK(d.ctrl, 3, at, 4ull * d.pool_quads) && block_fits(d, 4, x.off_l, x.lgs >> 8);
         const uint2 es = fits ? d.pool[at] : make_uint2(kEmptyId, kEmptyId);
         if (WORK && j == 0) { wk.entries += x.cnt_s; wk.slots += x.cnt_s; }
-        if (es.y < x.t && (!d.col || wedge_may_count(d, x.l, es.x, d.col[at]))) {
+        const uint32_t ws = es.x & id_mask(d);
+        if (es.y < x.t && (!d.colours || wedge_may_count(d, x.l, ws, es.x >> kIdBits))) {
             uint32_t nslots = 0;
-            const uint32_t tl = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, es.x, nslots);
+            const uint32_t tl = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, ws, nslots);
             if (WORK) { ++wk.probes; wk.pslots += nslots; }
             has = tl < x.t;  // kEmptyId (absent) is never < t
-            w = es.x;
+            w = ws;
         }
     }
     mq_push<WORK>(d, mq, has, x.s, x.l, w, s_proc, wk);
@@ -625,27 +622,23 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
           block_fits(d, 7, x.off_l, lg_l)))
         return;  // (uniform over the warp: x is)
     // the smaller endpoint's entry list (32-byte aligned), read 128 entries per pass, two per 16-byte
-    // load; their colours (when kept) two per 2-byte load
+    // load; with colours, each entry's id and colour share its first word
     const unsigned long long at_s = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu));
     const uint4* list = reinterpret_cast<const uint4*>(d.pool + at_s);
-    const uint16_t* cols = COLOURED && d.col ? reinterpret_cast<const uint16_t*>(d.col + at_s) : nullptr;
+    const bool cols = COLOURED && d.colours;
+    const uint32_t mask = id_mask(d);
     const uint32_t* keys_l = reinterpret_cast<const uint32_t*>(d.pool + base_l);
     const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
     const uint32_t cap_l = 1u << lg_l;
     const unsigned below = (1u << lane) - 1u;
-    // COLOURED: the next pass's entries and colours are loaded while the current pass is tested
+    // COLOURED: the next pass's entries are loaded while the current pass is tested
     uint4 nq[2];
-    uint32_t nc[2];
     auto load_pass = [&](uint32_t j0) {
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
             const uint32_t jj = j0 + 64u * half + 2u * lane;
             nq[half] = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-            nc[half] = 0u;
-            if (jj < n_s) {
-                nq[half] = list[jj >> 1];
-                if (cols) nc[half] = cols[jj >> 1];
-            }
+            if (jj < n_s) nq[half] = list[jj >> 1];
         }
     };
     if (COLOURED) load_pass(0u);
@@ -654,22 +647,21 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
         if (!REPT_CHECK(d.ctrl, 8, n_q, kRound)) break;
         if (!COLOURED) load_pass(j0);
         const uint4 cq[2] = {nq[0], nq[1]};
-        const uint32_t cc[2] = {nc[0], nc[1]};
         if (COLOURED && j0 + 128u < n_s) load_pass(j0 + 128u);
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
             const uint32_t jj = j0 + 64u * half + 2u * lane;
             const uint4 q = cq[half];
-            const uint32_t c2 = cc[half];
+            const uint32_t w1 = q.x & mask, w2 = q.z & mask;
             bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
-            if (COLOURED && cols) {
-                a1 = a1 && wedge_may_count(d, x.l, q.x, c2 & 0xFFu);
-                a2 = a2 && wedge_may_count(d, x.l, q.z, c2 >> 8);
+            if (cols) {
+                a1 = a1 && wedge_may_count(d, x.l, w1, q.x >> kIdBits);
+                a2 = a2 && wedge_may_count(d, x.l, w2, q.z >> kIdBits);
             }
             const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
-            if (a1) queue[n_q + __popc(m1 & below)] = q.x;
+            if (a1) queue[n_q + __popc(m1 & below)] = w1;
             n_q += __popc(m1);
-            if (a2) queue[n_q + __popc(m2 & below)] = q.z;
+            if (a2) queue[n_q + __popc(m2 & below)] = w2;
             n_q += __popc(m2);
         }
         __syncwarp();
@@ -989,10 +981,11 @@ __device__ __forceinline__ void group_drain_tiles(const StreamDev* __restrict__ 
                     const bool fits = REPT_CHECK(d.ctrl, 3, at, 4ull * d.pool_quads) &&
                                       block_fits(d, 4, x.off_l, x.lgs >> 8);
                     const uint2 es = fits ? d.pool[at] : make_uint2(kEmptyId, kEmptyId);
-                    if (es.y < x.t && (!d.col || wedge_may_count(d, x.l, es.x, d.col[at]))) {
+                    const uint32_t ws = es.x & id_mask(d);
+                    if (es.y < x.t && (!d.colours || wedge_may_count(d, x.l, ws, es.x >> kIdBits))) {
                         uint32_t nslots = 0;
-                        has = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, es.x, nslots) < x.t;
-                        w = es.x;
+                        has = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, ws, nslots) < x.t;
+                        w = ws;
                     }
                 }
             }

@@ -150,9 +150,10 @@ def test_fixed_pool_capacity_error():
     assert found
 
 
-def test_large_node_ids():
-    """Ids near the top of a 2^27-node space (meta/local arrays of 1-2 GB)."""
-    n = 1 << 27
+@pytest.mark.parametrize("n", [1 << 24, 1 << 27])
+def test_large_node_ids(n):
+    """Ids near the top of a 2^24-node space (the largest whose list entries carry colours in their
+    top 8 bits) and of a 2^27-node space (no colours kept; meta/local arrays of 1-2 GB)."""
     base = gg.gnp(60, 0.25, 16, 17)
     off = np.uint32(n - 64)
     s = gg.EdgeStream(base.src + off, base.dst + off, n)
