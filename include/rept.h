@@ -109,7 +109,8 @@ typedef struct rept_stats {
     /* with REPT_FLAG_WORK_COUNTERS, totals over the stream's intersection passes: */
     uint64_t small_entries;  /* entries present in the smaller endpoint's table, summed over edges */
     uint64_t small_slots;    /* slots of those tables read (entries plus empty slots) */
-    uint64_t probes;         /* probes of the larger endpoint's table (small-side entries older than the edge) */
+    uint64_t probes;         /* probes of the larger endpoint's table (small-side entries older than the edge
+                                and, where colours are kept, coloured alike for a kept processor) */
     uint64_t probe_slots;    /* slots read by those probes */
     uint64_t wedges;         /* closed wedges found in the union adjacency (both edges older than the edge) */
     uint64_t counted;        /* (wedge, hash group) pairs counted for some processor */
@@ -129,6 +130,11 @@ typedef struct rept_state rept_state;
  * n_nodes == 0; REPT_E_NOMEM / REPT_E_CUDA on allocation failure.  For c > m
  * with c mod m != 0 the handle also keeps Algorithm 2's triangle-pair
  * counters (16 + 12 * ceil(c/m) bytes per stream edge).
+ * Speed: with one hash group (c <= m, or MASCOT with c == 1), 2 <= m <= 256
+ * and n_nodes <= 2^24, each stored entry keeps its colour, and the
+ * intersection tests colours before it looks an edge up, so only about 1/m
+ * of the lookups happen; other configurations look up every candidate wedge
+ * edge (same counts, slower intersection).
  */
 int rept_create(const rept_config* cfg, void* stream, rept_state** out);
 
