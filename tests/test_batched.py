@@ -98,3 +98,24 @@ def test_ingest_multi_equals_the_oracle():
     finally:
         for h in handles:
             h.close()
+
+
+def test_autotune_picks_the_fastest_and_caches(tmp_path, monkeypatch):
+    """Host logic of the autotuner with a fake timing: the fastest (batch, tile) wins, the choice is
+    written to the cache, and a second call reads it back without timing anything."""
+    calls = []
+
+    def fake_run(streams, params, batch, tile_max, **kw):
+        calls.append((batch, tile_max))
+        return None, abs(batch - (1 << 18)) / 1e6 + (0.5 if tile_max == 16 else 0.1)
+
+    monkeypatch.setattr(batched, "run_batched", fake_run)
+    monkeypatch.setattr(batched, "_device_key", lambda: "fake-gpu")
+    monkeypatch.setattr(batched, "_CACHE", str(tmp_path / "autotune.json"))
+    b, tm, timings = batched.autotune([], [], key="t", repeat=1)
+    assert (b, tm) == (1 << 18, 32) and len(timings) == 6 and len(calls) == 6
+    b2, tm2, t2 = batched.autotune([], [], key="t", repeat=1)
+    assert (b2, tm2) == (b, tm) and t2 == timings and len(calls) == 6   # served from the cache
+    (tmp_path / "autotune.json").write_text("{not json")
+    b3, _, _ = batched.autotune([], [], key="t", repeat=1)            # a damaged cache is re-measured
+    assert b3 == 1 << 18 and len(calls) == 12
