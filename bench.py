@@ -200,7 +200,7 @@ def cpu_sample_rate(s, m, c, budget_s=15.0):
 # DRAM bytes (read + write) per k_intersect launch, the mean over the 15 launches of one step from an
 # ncu capture of the current kernel (profiles/k_intersect_rmat_s20_c100.md); absent for workloads not
 # captured.  Must be removed when the kernel changes.
-K3_TRAFFIC = {("rmat_s20", 100): 786.7e6}
+K3_TRAFFIC = {}
 
 
 # --------------------------------------------------------------------------- reference arm

@@ -104,9 +104,9 @@ __host__ __device__ __forceinline__ uint32_t fast_mod(uint64_t x, const FastMod&
 // m = q * 2^k (q odd), n is a multiple of m exactly when (n * q^-1 mod 2^64) rotated right by k is at
 // most floor((2^64 - 1) / m) (Granlund and Montgomery, "Division by invariant integers using
 // multiplication", 1994, Section 9): one 64-bit multiply instead of a remainder.
-__host__ __device__ __forceinline__ bool mod_equals(uint64_t x, uint32_t j, const FastMod& f) {
-    if (f.m < 2) return j == 0u;
-    if (j >= f.m || x < j) return false;
+// mod_equals_in_range assumes m >= 2 and j < m; mod_equals takes any m and j.
+__host__ __device__ __forceinline__ bool mod_equals_in_range(uint64_t x, uint32_t j, const FastMod& f) {
+    if (x < j) return false;
     const uint64_t y = (x - j) * f.qinv;
 #ifdef __CUDA_ARCH__
     // rotate right by k < 32 (m < 2^32): each half is a funnel shift of the two halves
@@ -116,6 +116,12 @@ __host__ __device__ __forceinline__ bool mod_equals(uint64_t x, uint32_t j, cons
     const uint64_t r = (y >> f.k) | (y << ((64u - f.k) & 63u));
 #endif
     return r <= f.lim;
+}
+
+__host__ __device__ __forceinline__ bool mod_equals(uint64_t x, uint32_t j, const FastMod& f) {
+    if (f.m < 2) return j == 0u;
+    if (j >= f.m) return false;
+    return mod_equals_in_range(x, j, f);
 }
 
 struct Ctrl {
@@ -235,10 +241,10 @@ __device__ __forceinline__ uint32_t colour_of(uint32_t a, uint32_t b, uint64_t s
 
 __device__ __forceinline__ uint64_t group_seed(uint64_t seed, uint32_t k) { return seed + (uint64_t)k * kGoldenGamma; }
 
-// h_k({a, b}) == j, for a colour j < m.
+// h_k({a, b}) == j, for m >= 2 and a colour j < m.
 __device__ __forceinline__ bool colour_is(uint32_t a, uint32_t b, uint64_t s_k, const FastMod& fm, uint32_t j) {
     uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
-    return mod_equals(splitmix64(((lo << 32) | hi) ^ s_k), j, fm);
+    return mod_equals_in_range(splitmix64(((lo << 32) | hi) ^ s_k), j, fm);
 }
 
 // Is edge {u, v} kept by some processor (k*m + h_k(u,v) < c for some group k)?

@@ -295,7 +295,18 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
         uint32_t u = 0, v = 0;
         if (valid) { u = b.src[e]; v = b.dst[e]; }
         const bool loop = valid && u == v;
-        const bool kept = valid && u != v && kept_by_any(d, u, v);
+        // with colours (one hash group) the edge's colour decides whether it is kept and rides in its
+        // list entries: one hash serves both
+        uint32_t cj = 0u;
+        bool kept;
+        if (d.colours) {
+            uint32_t i;
+            const uint32_t j = colour_of(u, v, d.seed, d.fm);
+            kept = valid && u != v && processor_of(d, 0u, j, i);
+            cj = j << kIdBits;
+        } else {
+            kept = valid && u != v && kept_by_any(d, u, v);
+        }
         uint32_t key = kNoKey;
         WorkItem it{};
         if (valid && u != v) {
@@ -309,8 +320,6 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
                 // list positions: add[x] counts this batch's entries of x back down to zero
                 const uint32_t pu = mu.y - atomicSub(&d.add[u], 1u), pv = mv.y - atomicSub(&d.add[v], 1u);
                 if (REPT_CHECK(ct, 2, pu, list_slots(lu)) && REPT_CHECK(ct, 2, pv, list_slots(lv))) {
-                    // with colours, h_0(u, v) rides in the top bits of both entries
-                    const uint32_t cj = d.colours ? colour_of(u, v, d.seed, d.fm) << kIdBits : 0u;
                     d.pool[4ull * mu.x + (1ull << lu) + pu] = make_uint2(v | cj, t);
                     d.pool[4ull * mv.x + (1ull << lv) + pv] = make_uint2(u | cj, t);
                 }
