@@ -200,7 +200,7 @@ def cpu_sample_rate(s, m, c, budget_s=15.0):
 # DRAM bytes (read + write) per k_intersect launch, the mean over the 15 launches of one step from an
 # ncu capture of the current kernel (profiles/k_intersect_rmat_s20_c100.md); absent for workloads not
 # captured.  Must be removed when the kernel changes.
-K3_TRAFFIC = {}
+K3_TRAFFIC = {("rmat_s20", 100): 786.7e6}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -378,8 +378,8 @@ def run_ours(args, world, rank, local, pg):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": K3_TRAFFIC.get((args.workload, c)),
                          "kernel": "k_intersect",
-                         "limiter": "integer issue where colours are kept (ncu: 77 % issue active, ALU pipe "
-                                    "67 %, DRAM 9 %); algorithmic bytes understate the kernel's load",
+                         "limiter": "integer issue where colours are kept (ncu: 76 % issue active, ALU pipe "
+                                    "66 %, DRAM 9 %); algorithmic bytes understate the kernel's load",
                          "peak_source": peak_src, "algorithmic_bytes_per_step": k3_bytes,
                          "kernel_ms_per_step": k3_ms_step, "launches_per_step": k3_n // args.steps},
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
