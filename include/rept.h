@@ -54,7 +54,8 @@ extern "C" {
 #define REPT_E_CAPACITY (-3)  /* REPT_FLAG_FIXED_POOL set and the adjacency pool is full (batch not applied) */
 #define REPT_E_NOMEM (-4)     /* a device or pinned-host allocation failed */
 #define REPT_E_CUDA (-5)      /* a CUDA runtime call failed */
-#define REPT_E_TIMEOUT (-6)   /* a bounded device-side wait gave up (batched persistent path) */
+#define REPT_E_TIMEOUT (-6)   /* reserved for a bounded device-side wait that gives up; no kernel of this
+                                 library waits on a flag or on another kernel, so none returns it */
 #define REPT_E_INTERNAL (-7)  /* a device-side invariant failed (bounded probe found no slot) */
 #define REPT_E_SCRATCH (-8)   /* rept_count_noalloc: the problem does not fit its fixed scratch area */
 #define REPT_E_DUPLICATE (-9) /* REPT_FLAG_CHECK_DUPS: a repeated edge (device-detected, batch not applied) */
