@@ -339,7 +339,11 @@ int rept_ingest_multi(rept_state* const* hs, const uint32_t* const* d_src, const
  *
  * Behaviour: the first call on a device looks up the scratch array's device
  * address on that device (cudaGetSymbolAddress) and caches it; make that first
- * call before any stream capture.  Every call enqueues its work on `stream`,
+ * call before any stream capture.  Later calls on a stream that is not being
+ * captured look the address up again, so a cudaDeviceReset between calls
+ * (which reloads the library's device code) is safe; a call inside a capture
+ * uses the cached address, so no device reset may happen between the last
+ * uncaptured call and a capture.  Every call enqueues its work on `stream`,
  * then waits for the stream and returns REPT_E_RANGE if an endpoint was
  * >= n_nodes (outputs then undefined).  All calls share the one scratch array
  * and the call clears the parts that must start at zero, so sequential calls

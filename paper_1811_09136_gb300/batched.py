@@ -185,43 +185,73 @@ def _collect(h, local_estimates):
                         None if loc is None else loc.cpu().numpy())
 
 
+def _pinned(a: np.ndarray):
+    import torch
+    return torch.from_numpy(a.view(np.int32)).pin_memory()
+
+
+def _result_buffers(c: int):
+    """Pinned host buffers for rept_estimates_async: tau_hat, tau^(i), status word."""
+    import torch
+    return (torch.empty(1, dtype=torch.float64).pin_memory().numpy(),
+            torch.empty(c, dtype=torch.int64).pin_memory().numpy().view(np.uint64),
+            torch.empty(1, dtype=torch.int32).pin_memory().numpy().view(np.uint32))
+
+
 def run_batched(streams, params, batch: int = 1 << 18, tile_max: int = 32, graph: bool = True,
-                budget: int | None = None, local_estimates: bool = False, presize: bool = True):
+                budget: int | None = None, local_estimates: bool = False, presize: bool = True,
+                host_io: bool = False):
     """All streams through one rept_group, batch edges per stream per round.  `params[i]` is
     (m, c, seed).  With `presize` every pool is sized for its whole stream up front (no round needs
-    a pool check); without it pools start small and grow (one host check per round).  Returns
-    (results, seconds of device work incl. per-round host launch cost)."""
+    a pool check); without it pools start small and grow (one host check per round).  With
+    `host_io` the timed region also holds the copy of every stream's edges from pinned host memory
+    to the device and the copy of each stream's tau_hat, tau^(i) and status word back to pinned
+    host memory (end to end).  Returns (results, seconds of device work incl. per-round host launch
+    cost)."""
     import torch
     budget = budget or _device_budget()
     results = [None] * len(streams)
     total = 0.0
     for wave in _waves(streams, batch, budget):
-        handles, srcs, dsts = [], [], []
+        handles, srcs, dsts, hsrc, hdst, outs = [], [], [], [], [], []
         for i in wave:
             s = streams[i]
             m, c, seed = params[i]
             handles.append(rept.ReptStream(s.n_nodes, m, c, seed, expected_edges=len(s) if presize else 0,
                                            max_batch=min(batch, max(1, len(s))), tile_max=tile_max))
-            srcs.append(torch.from_numpy(s.src.view(np.int32)).cuda())
-            dsts.append(torch.from_numpy(s.dst.view(np.int32)).cuda())
+            if host_io:
+                hsrc.append(_pinned(s.src))
+                hdst.append(_pinned(s.dst))
+                outs.append(_result_buffers(c))
+            else:
+                srcs.append(torch.from_numpy(s.src.view(np.int32)).cuda())
+                dsts.append(torch.from_numpy(s.dst.view(np.int32)).cuda())
         group = ReptGroup(len(wave), graph=graph)
         rounds = max((len(streams[i]) + batch - 1) // batch for i in wave)
         torch.cuda.synchronize()
         t = time.perf_counter()
+        if host_io:
+            srcs = [x.to("cuda", non_blocking=True) for x in hsrc]
+            dsts = [x.to("cuda", non_blocking=True) for x in hdst]
         for r in range(rounds):
             # only the streams that still have edges take part, so the finished ones free their SMs
             live = [j for j, x in enumerate(srcs) if r * batch < x.numel()]
             group.ingest([handles[j] for j in live], [srcs[j][r * batch:(r + 1) * batch] for j in live],
                          [dsts[j][r * batch:(r + 1) * batch] for j in live])
+        if host_io:
+            for h, o in zip(handles, outs):
+                h.estimates_async(*o)
         for h in handles:
             h.sync()
         torch.cuda.synchronize()
         total += time.perf_counter() - t
         for j, i in enumerate(wave):
+            if host_io:
+                assert int(outs[j][2][0]) == 0, "device error"
             results[i] = _collect(handles[j], local_estimates)
             handles[j].close()
         group.close()
-        del srcs, dsts
+        del srcs, dsts, hsrc, hdst
     return results, total
 
 

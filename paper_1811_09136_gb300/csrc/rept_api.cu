@@ -44,16 +44,6 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
         }                                                 \
     } while (0)
 
-int status_to_code(unsigned st) {
-    if (st & kStRange) return REPT_E_RANGE;
-    if (st & kStCapacity) return REPT_E_CAPACITY;
-    if (st & kStTimeout) return REPT_E_TIMEOUT;
-    if (st & kStInternal) return REPT_E_INTERNAL;
-    if (st & kStDuplicate) return REPT_E_DUPLICATE;
-    if (st & kStBounds) return REPT_E_INTERNAL;
-    return REPT_OK;
-}
-
 }  // namespace
 
 struct rept_state {
@@ -328,9 +318,7 @@ int sync_status(rept_state* s, cudaStream_t st) {
     int rc = read_ctrl(s, st);
     if (rc) return rc;
 #ifdef REPT_DEBUG_BOUNDS
-    if (s->h_ctrl->dbg[3])
-        std::fprintf(stderr, "rept: index check at site %llu failed: index %llu, bound %llu (%llu failures)\n",
-                     s->h_ctrl->dbg[0], s->h_ctrl->dbg[1], s->h_ctrl->dbg[2], s->h_ctrl->dbg[3]);
+    report_failed_check(s->h_ctrl->dbg);
 #endif
     return status_to_code(s->h_ctrl->status);
 }

@@ -24,6 +24,9 @@
 #pragma once
 
 #include <cstdint>
+#include <cstdio>
+
+#include "rept.h"
 
 namespace rept {
 
@@ -46,6 +49,26 @@ constexpr uint16_t kNoKey = 0xFFFFu;
 // status bits (sticky)
 constexpr unsigned kStRange = 1u, kStCapacity = 2u, kStInternal = 4u, kStTimeout = 8u, kStDuplicate = 16u;
 constexpr unsigned kStBounds = 32u;  // REPT_DEBUG_BOUNDS builds: an index check failed
+
+// The REPT_E_* code (rept.h) that a sticky status word reports, most specific condition first.  A
+// failed index check of the REPT_DEBUG_BOUNDS build is an internal error.
+inline int status_to_code(unsigned st) {
+    if (st & kStRange) return REPT_E_RANGE;
+    if (st & kStCapacity) return REPT_E_CAPACITY;
+    if (st & kStTimeout) return REPT_E_TIMEOUT;
+    if (st & kStInternal) return REPT_E_INTERNAL;
+    if (st & kStDuplicate) return REPT_E_DUPLICATE;
+    if (st & kStBounds) return REPT_E_INTERNAL;
+    return REPT_OK;
+}
+
+// REPT_DEBUG_BOUNDS builds: print the first failed index check ({site, index, bound, failures}, the
+// `dbg` words of the control block) to stderr.
+inline void report_failed_check(const unsigned long long* dbg) {
+    if (dbg[3])
+        std::fprintf(stderr, "rept: index check at site %llu failed: index %llu, bound %llu (%llu failures)\n",
+                     dbg[0], dbg[1], dbg[2], dbg[3]);
+}
 
 // x mod m for 64-bit x and 32-bit m >= 2 without a division: Lemire, Kaser, Kurz, "Faster Remainder
 // by Direct Computation" (2019).  With the 128-bit magic M = floor((2^128 - 1) / m) + 1, the low 128

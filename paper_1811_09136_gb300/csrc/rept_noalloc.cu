@@ -49,17 +49,28 @@ Layout layout_for(unsigned long long n, unsigned long long E) {
     return L;
 }
 
-int scratch_address(void** out) {
+// The device address of g_scratch on the current device.  Set-up, once per device with that device
+// current: look the symbol up and cache it.  Later calls outside a stream capture look it up again
+// (a cheap query), so that after cudaDeviceReset, which reloads the module and may move the array,
+// no kernel is launched on a stale address; inside a capture the cached address is used, because
+// the lookup may not be legal there.
+int scratch_address(cudaStream_t st, void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return REPT_E_CUDA;
     void* p = g_scratch_addr[dev].load(std::memory_order_acquire);
-    if (!p) {
-        // set-up, once per device, with that device current
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (p && cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;  // unknown: keep the cached address
+    }
+    if (!p || cap == cudaStreamCaptureStatusNone) {
+        void* q = nullptr;
+        if (cudaGetSymbolAddress(&q, g_scratch) != cudaSuccess || !q) {
             (void)cudaGetLastError();
             return REPT_E_CUDA;
         }
-        g_scratch_addr[dev].store(p, std::memory_order_release);
+        if (q != p) g_scratch_addr[dev].store(q, std::memory_order_release);
+        p = q;
     }
     *out = p;
     return REPT_OK;
@@ -85,10 +96,10 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
     if (n_edges >= 0xFFFFFFFEull) return REPT_E_SCRATCH;
     const Layout L = layout_for(n_nodes, n_edges);
     if (L.end > REPT_NOALLOC_SCRATCH_BYTES) return REPT_E_SCRATCH;
-    void* base = nullptr;
-    int rc = scratch_address(&base);
-    if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    void* base = nullptr;
+    int rc = scratch_address(st, &base);
+    if (rc) return rc;
     unsigned char* sc = static_cast<unsigned char*>(base);
 
     StreamDev d{};
@@ -153,9 +164,16 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
     }
     unsigned int status = 0;
     NA_CUDA(cudaMemcpyAsync(&status, &d.ctrl->status, sizeof(status), cudaMemcpyDeviceToHost, st));
+#ifdef REPT_DEBUG_BOUNDS
+    unsigned long long dbg[4] = {0, 0, 0, 0};
+    NA_CUDA(cudaMemcpyAsync(dbg, d.ctrl->dbg, sizeof(dbg), cudaMemcpyDeviceToHost, st));
+#endif
     NA_CUDA(cudaStreamSynchronize(st));
-    if (status & kStRange) return REPT_E_RANGE;
-    if (status & kStCapacity) return REPT_E_INTERNAL;  // impossible: the pool is sized for the worst case
-    if (status & kStInternal) return REPT_E_INTERNAL;
-    return REPT_OK;
+#ifdef REPT_DEBUG_BOUNDS
+    report_failed_check(dbg);
+#endif
+    // the same mapping as the handle path, except that a full pool is internal here: the pool is
+    // sized for the worst case of an empty state
+    rc = status_to_code(status);
+    return rc == REPT_E_CAPACITY ? REPT_E_INTERNAL : rc;
 }

@@ -1,0 +1,50 @@
+"""One pass of a stream through the C ABI and nothing else: the command to run under a profiler.
+
+  python -m paper_1811_09136_gb300.profile_case --workload rmat_s20 --m 100 --c 100
+  python -m paper_1811_09136_gb300.profile_case --chung-lu 1048576 2.1 16777216 50000 --m 20 --c 100
+
+The stream is ingested once in batches of --batch edges into a handle whose pool grows as needed, so
+that the device holds little beyond the state the stream needs.  Kernel launches per batch follow
+the library's launch order (classify, plan, commit, two block-move kernels, insert, two sort
+kernels, intersect), which is what a profiler's launch skip count (-s) refers to.  With --group K
+the same stream is fed as K streams with distinct hash seeds through one rept_group instead.
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default=None, help="a named workload of graphgen.cached")
+    ap.add_argument("--chung-lu", nargs=4, type=float, default=None, metavar=("N", "GAMMA", "EDGES", "CAP"))
+    ap.add_argument("--m", type=int, default=100)
+    ap.add_argument("--c", type=int, default=100)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=1 << 20)
+    ap.add_argument("--work", action="store_true", help="with work counters (REPT_FLAG_WORK_COUNTERS)")
+    args = ap.parse_args()
+
+    import torch
+    from . import graphgen, rept
+
+    if args.chung_lu:
+        n, gamma, e, cap = args.chung_lu
+        s = graphgen.chung_lu(int(n), gamma, int(e), cap=cap)
+    else:
+        s = graphgen.cached(args.workload or "rmat_s20")
+    src = torch.from_numpy(s.src.view(np.int32)).cuda()
+    dst = torch.from_numpy(s.dst.view(np.int32)).cuda()
+    flags = rept.FLAG_WORK_COUNTERS if args.work else 0
+    with rept.ReptStream(s.n_nodes, args.m, args.c, args.seed, max_batch=args.batch, flags=flags) as r:
+        for off in range(0, len(s), args.batch):
+            r.ingest(src[off:off + args.batch], dst[off:off + args.batch])
+        proc, _ = r.counts()
+        st = r.stats()
+    print(f"{len(s)} edges, {int(proc.sum())} semi-triangles, pool {st['pool_used']} slots used", flush=True)
+
+
+if __name__ == "__main__":
+    main()

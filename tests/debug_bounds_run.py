@@ -65,7 +65,10 @@ def main():
     torch.cuda.synchronize()
     assert rc == 0, rc
     ref = O.rept_stream(st.src, st.dst, st.n_nodes, 10, 10, 4, pair_counters=False)
+    ref_g, _ = O.estimates(10, 10, ref, st.n_nodes)
     assert np.array_equal(proc.cpu().numpy().view(np.uint64), ref.tau_proc)
+    assert np.array_equal(local.cpu().numpy().view(np.uint64), ref.local1)
+    assert abs(float(g.item()) - ref_g) <= 1e-12 * abs(ref_g), (float(g.item()), ref_g)
     print("debug-bounds ok")
 
 

@@ -312,6 +312,55 @@ def pin_partial_group_statistics(lib=None):
     assert abs(eta_hats.mean() - eta) < 4.5 * eta_hats.std(ddof=1) / math.sqrt(R) + 1e-9
 
 
+def pin_partial_group_local_statistics(lib=None):
+    """c > m with c mod m != 0 (Algorithm 2), per node: over 400 spread hash seeds, on the three
+    nodes with the most triangles,
+      - the full groups' local estimate (m / c1) * local1[v] and the partial group's
+        (m^2 / c2) * local2[v] are unbiased for tau_v (Section III-B.2),
+      - the combined local estimate is unbiased and its variance is at most 1.2 * tau_v (m-1) / c1
+        (the full groups' variance; the combination only adds an independent estimate), and
+      - the eta_v estimate that the combination used is unbiased for the exact eta_v.
+    The last one is read back from the combination itself: with a1, a2 the two group estimates and
+    est their combination (w2 a1 + w1 a2) / (w1 + w2), the weight ratio is r = w1 / w2 =
+    (a1 - est) / (est - a2); w1 = a1 (m-1) / c1 gives w2 = w1 / r, and Section III-B.2's
+    w2 = (a1 (m^2 - c2) + 2 eta_hat_v (m - c2)) / c2 gives eta_hat_v.  Seeds where a1 = 0 or the
+    two estimates coincide carry no information and are skipped."""
+    s = gg.gnp(30, 0.5, 31, 32)
+    e = O.semitriangles(s.src, s.dst, 30, 1, 1, 1, lib=lib)
+    nodes = [int(x) for x in np.argsort(-e.tri_local.astype(np.int64), kind="stable")[:3]]
+    for (m, c) in [(3, 7), (4, 9)]:
+        c1, c2 = c // m, c % m
+        a1s, a2s, ests, eta_hats = [], [], [], []
+        for seed in _spread_seeds(400, 4):
+            a = O.rept_stream(s.src, s.dst, 30, m, c, seed, lib=lib)
+            _, loc = O.estimates(m, c, a, 30, lib=lib)
+            a1 = a.local1[nodes].astype(np.float64) * m / c1
+            a2 = a.local2[nodes].astype(np.float64) * m * m / c2
+            a1s.append(a1)
+            a2s.append(a2)
+            ests.append(loc[nodes])
+            row = np.full(len(nodes), np.nan)
+            for j in range(len(nodes)):
+                if a1[j] > 0 and abs(a1[j] - a2[j]) > 1e-9 * a1[j] and abs(loc[nodes[j]] - a2[j]) > 1e-9 * a1[j]:
+                    r = (a1[j] - loc[nodes[j]]) / (loc[nodes[j]] - a2[j])
+                    w2 = a1[j] * (m - 1) / c1 / r
+                    row[j] = (w2 * c2 - a1[j] * (m * m - c2)) / (2 * (m - c2))
+            eta_hats.append(row)
+        a1s, a2s, ests, eta_hats = map(np.array, (a1s, a2s, ests, eta_hats))
+        R = a1s.shape[0]
+        for j, v in enumerate(nodes):
+            tv, ev = int(e.tri_local[v]), int(e.eta_local[v])
+            var1 = tv * (m - 1) / c1
+            var2 = (tv * (m * m - c2) + 2 * ev * (m - c2)) / c2
+            assert abs(a1s[:, j].mean() - tv) < 4.5 * math.sqrt(var1 / R), (m, c, v, a1s[:, j].mean(), tv)
+            assert abs(a2s[:, j].mean() - tv) < 4.5 * math.sqrt(var2 / R), (m, c, v, a2s[:, j].mean(), tv)
+            assert abs(ests[:, j].mean() - tv) < 4.5 * math.sqrt(var1 / R), (m, c, v, ests[:, j].mean(), tv)
+            assert ests[:, j].var(ddof=1) < 1.2 * var1, (m, c, v, ests[:, j].var(ddof=1), var1)
+            eh = eta_hats[:, j][~np.isnan(eta_hats[:, j])]
+            assert eh.size > R // 2, (m, c, v, eh.size)
+            assert abs(eh.mean() - ev) < 4.5 * eh.std(ddof=1) / math.sqrt(eh.size) + 1e-9, (m, c, v, eh.mean(), ev)
+
+
 def pin_mascot_brute_force(lib=None):
     """Parallel MASCOT (Section III-C): sampler i stores an edge iff hash group i colours it 0, and
     counts a triangle iff its two earliest edges are both stored.  The streaming and static oracles
@@ -373,5 +422,5 @@ def pin_mascot_statistics(lib=None):
 ALL_PINS = [pin_splitmix64_published, pin_colour_uniform, pin_brute_force, pin_complete_graph,
             pin_local_sum_invariant, pin_count_before_insert, pin_self_loops, pin_networkx_triangles,
             pin_eta_exact_at_m1, pin_batch_split_and_static, pin_theorem3_statistics,
-            pin_partial_group_statistics, pin_mascot_brute_force, pin_mascot_complete_graph,
+            pin_partial_group_statistics, pin_partial_group_local_statistics, pin_mascot_brute_force, pin_mascot_complete_graph,
             pin_mascot_statistics]

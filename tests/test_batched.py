@@ -119,3 +119,35 @@ def test_autotune_picks_the_fastest_and_caches(tmp_path, monkeypatch):
     (tmp_path / "autotune.json").write_text("{not json")
     b3, _, _ = batched.autotune([], [], key="t", repeat=1)            # a damaged cache is re-measured
     assert b3 == 1 << 18 and len(calls) == 12
+
+
+@pytest.mark.gpu
+def test_batched_midsize_stream_runs_the_hub_classes_and_matches_the_oracle():
+    """A mix with one mid-size power-law stream (2 x 10^5 nodes, 2.4 x 10^6 edges) beside small ones:
+    its smaller endpoints reach hundreds of entries, so the warp classes (33-256 entries and more)
+    run inside the group's intersection kernel; every stream's counts equal the oracle's static
+    enumeration and the plain path's."""
+    from paper_1811_09136_gb300 import graphgen as gg
+    from paper_1811_09136_gb300 import rept
+    import torch
+    big = gg.chung_lu(200_000, 2.1, 2_400_000, cap=20_000.0, graph_seed=61, order_seed=62)
+    small, sparams = _mix(k=3, seed=29)
+    streams = [big] + small
+    params = [(20, 20, 4242)] + sparams
+    # the big stream really has edges of both warp classes
+    with rept.ReptStream(big.n_nodes, 20, 20, 4242, max_batch=1 << 18, flags=rept.FLAG_WORK_COUNTERS) as r:
+        src = torch.from_numpy(big.src.view(np.int32)).cuda()
+        dst = torch.from_numpy(big.dst.view(np.int32)).cuda()
+        for off in range(0, len(big), 1 << 18):
+            r.ingest(src[off:off + (1 << 18)], dst[off:off + (1 << 18)])
+        st = r.stats()
+    assert st["class_items"][4] > 0 and st["class_items"][5] > 0, st["class_items"]
+    res_b, _ = batched.run_batched(streams, params, batch=1 << 18, graph=True)
+    res_p, _ = batched.run_plain(streams, params, batch=1 << 18)
+    for s, (m, c, seed), rb, rp in zip(streams, params, res_b, res_p):
+        ref = O.semitriangles(s.src, s.dst, s.n_nodes, m, c, seed)
+        ref_g, _ = O.estimates(m, c, O.Counts(ref.tau_proc, ref.local1, ref.local2), s.n_nodes)
+        for r in (rb, rp):
+            assert np.array_equal(r.proc, ref.tau_proc)
+            assert np.array_equal(r.local, ref.local1)
+            assert abs(r.tau_hat - ref_g) <= 1e-12 * max(abs(ref_g), 1.0)

@@ -45,3 +45,28 @@ def test_reference_arm_two_ranks_rank0_prints():
     lines = [l for l in out.stdout.strip().splitlines() if l.startswith("{")]
     assert len(lines) == 1, out.stdout
     _check(json.loads(lines[0]), 1, 1)
+
+
+def test_oracle_comparison_of_timed_counts():
+    """bench.compare_with_oracle: identical counts pass; one changed tau^(i), one changed local
+    count, an estimate off by more than 1e-12 relative, or another input each fail."""
+    import hashlib
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1811_09136_gb300 import graphgen as gg
+    s = gg.gnp(30, 0.3, 5, 6)
+    proc = np.array([3, 0, 7], dtype=np.uint64)
+    local = np.arange(30, dtype=np.uint64)
+    dig = {"k": {"input_sha256": s.sha256(), "tau_proc": ["3", "0", "7"],
+                 "local_sha256": hashlib.sha256(local.astype("<u8").tobytes()).hexdigest(),
+                 "tau_hat": (1234.5).hex()}}
+    assert bench.compare_with_oracle(dig, "k", s, proc, local, 1234.5)["identical"]
+    assert not bench.compare_with_oracle(dig, "k", s, proc + np.uint64(1), local, 1234.5)["identical"]
+    bad = local.copy()
+    bad[7] += np.uint64(1)
+    assert not bench.compare_with_oracle(dig, "k", s, proc, bad, 1234.5)["identical"]
+    assert not bench.compare_with_oracle(dig, "k", s, proc, local, 1234.5 * (1 + 1e-11))["identical"]
+    assert bench.compare_with_oracle(dig, "k", s, proc, local, 1234.5 * (1 + 1e-13))["identical"]
+    assert not bench.compare_with_oracle(dig, "k", gg.gnp(30, 0.3, 5, 7), proc, local, 1234.5)["checked"]
+    assert not bench.compare_with_oracle(dig, "other", s, proc, local, 1234.5)["checked"]

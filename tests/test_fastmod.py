@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 def test_fast_mod_matches_percent(tmp_path):
     exe = str(tmp_path / "fastmod_check")
-    subprocess.check_call([_build._nvcc(), "-O2", "-std=c++17", "-I", _build.CSRC, "-o", exe,
+    subprocess.check_call([_build._nvcc(), "-O2", "-std=c++17", "-I", _build.CSRC, "-I", _build.INCLUDE, "-o", exe,
                            os.path.join(HERE, "native", "fastmod_check.cu")])
     out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stdout + out.stderr

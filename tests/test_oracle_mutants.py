@@ -27,6 +27,12 @@ MUTANTS = {
     "mascot_samplers_share_hash": ("*k = mascot ? i : i / m;", "*k = mascot ? 0 : i / m;"),
     "mascot_keeps_colour_i": ("*j = mascot ? 0 : i % m;", "*j = mascot ? i % m : i % m;"),
     "mascot_scale_p_not_p2": ("double inv_p2 = md * md;", "double inv_p2 = md;"),
+    "local_weights_swapped": ("est_local[v] = (v1 + v2 > 0.0) ? (v2 * a1 + v1 * a2) / (v1 + v2) : a1;",
+                              "est_local[v] = (v1 + v2 > 0.0) ? (v1 * a1 + v2 * a2) / (v1 + v2) : a1;"),
+    "local_eta_scaled_m2": ("double eh = (double)eta_local[v] * (md * md * md / (double)c);",
+                            "double eh = (double)eta_local[v] * (md * md / (double)c);"),
+    "local2_scale_full_groups": ("double a1 = (double)local1[v] * f1, a2 = (double)local2[v] * f2;",
+                                 "double a1 = (double)local1[v] * f1, a2 = (double)local2[v] * f1;"),
 }
 
 

@@ -1,8 +1,21 @@
-"""Serving with continuous batching: every request's result is the same as counting it alone."""
+"""Serving with continuous batching: every request's result is the oracle's, and the same as counting
+it alone."""
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1811_09136_gb300 import batched, serve
+
+
+def _assert_oracle(r):
+    """The served request's tau^(i), local counts and tau_hat against the sequential oracle."""
+    s = r.stream
+    ref = O.rept_stream(s.src, s.dst, s.n_nodes, r.m, r.c, r.seed, pair_counters=False)
+    ref_g, _ = O.estimates(r.m, r.c, ref, s.n_nodes)
+    assert np.array_equal(r.proc, ref.tau_proc), r.rid
+    if r.local is not None:
+        assert np.array_equal(r.local, ref.local1), r.rid
+    assert abs(r.tau_hat - ref_g) <= 1e-12 * max(abs(ref_g), 1.0), (r.rid, r.tau_hat, ref_g)
 
 
 def test_poisson_arrivals_rate_and_determinism():
@@ -35,6 +48,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix(max_live, budget):
     assert len(rep.requests) == len(reqs)
     assert rep.max_live > 1                     # requests really overlapped on the device
     for r in rep.requests:
+        _assert_oracle(r)
         g, proc, local = serve.count_alone(r)
         assert np.array_equal(r.proc, proc)
         assert np.array_equal(r.local, local)
@@ -54,6 +68,7 @@ def test_reused_handles_give_the_same_results():
             for i in range(10)]
     rep = serve.serve(reqs, max_live=2, keep_local=True)
     for r in rep.requests:
+        _assert_oracle(r)
         g, proc, local = serve.count_alone(r)
         assert np.array_equal(r.proc, proc) and np.array_equal(r.local, local)
         assert abs(r.tau_hat - g) <= 1e-12 * max(abs(g), 1.0)
@@ -85,6 +100,7 @@ def test_cancelled_requests_leave_the_others_exact():
     assert all(np.isnan(r.tau_hat) for r in rep.cancelled)
     assert len(rep.requests) == len(reqs) - 2
     for r in rep.requests:
+        _assert_oracle(r)
         g, proc, local = serve.count_alone(r)
         assert np.array_equal(r.proc, proc) and np.array_equal(r.local, local)
         assert abs(r.tau_hat - g) <= 1e-12 * max(abs(g), 1.0)

@@ -4,7 +4,9 @@ Some callers cannot call cudaMalloc: their device memory is owned by another
 allocator, or they cannot afford the device-wide synchronisation that freeing
 memory implies.  rept_count_noalloc serves them by keeping all of its scratch in
 a fixed device array inside the library.  This test calls it through the C ABI
-twice in a row, on two different streams, and checks each result against the
+twice in a row, the first call on the current stream and the second on a stream
+of its own (the calls do not overlap: each waits for its stream before it
+returns), and checks each result against the
 regular handle-based entry points (rept_create / rept_ingest_batch /
 rept_counts / rept_estimates): the integer counts must be identical and the
 global estimate within 1e-12 relative, the tolerance of the other GPU tests.
@@ -33,8 +35,9 @@ def _lib():
     return fn
 
 
-def _noalloc(fn, s, m, c, seed):
+def _noalloc(fn, s, m, c, seed, stream=None):
     import torch
+    stream = stream or torch.cuda.current_stream()
     src = torch.from_numpy(s.src.view(np.int32)).cuda()
     dst = torch.from_numpy(s.dst.view(np.int32)).cuda()
     proc = torch.empty(c, dtype=torch.int64, device="cuda")
@@ -43,9 +46,11 @@ def _noalloc(fn, s, m, c, seed):
     # poison the outputs: the call must overwrite them
     proc.fill_(-1)
     local.fill_(-1)
-    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    # the inputs and poisoned outputs were written on the current stream
+    stream.wait_stream(torch.cuda.current_stream())
     rc = fn(src.data_ptr(), dst.data_ptr(), len(s), s.n_nodes, m, c, seed, proc.data_ptr(), local.data_ptr(),
-            glob.data_ptr(), stream)
+            glob.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+    torch.cuda.current_stream().wait_stream(stream)
     return rc, proc.cpu().numpy().view(np.uint64), local.cpu().numpy().view(np.uint64), float(glob.item())
 
 
@@ -68,8 +73,8 @@ def test_noalloc_matches_regular_entry_points_on_two_calls_in_a_row():
     fn = _lib()
     first = gg.chung_lu(20_000, 2.3, 200_000, graph_seed=42, order_seed=7)
     second = gg.chung_lu(50_000, 2.1, 120_000, cap=2_000.0, graph_seed=3, order_seed=4)
-    for s, (m, c, seed) in ((first, (10, 10, 1)), (second, (4, 8, 99))):
-        rc, proc, local, g = _noalloc(fn, s, m, c, seed)
+    for s, (m, c, seed), stream in ((first, (10, 10, 1), None), (second, (4, 8, 99), torch.cuda.Stream())):
+        rc, proc, local, g = _noalloc(fn, s, m, c, seed, stream)
         assert rc == 0, rc
         ref_proc, ref_local, ref_g = _regular(s, m, c, seed)
         assert np.array_equal(proc, ref_proc)
@@ -81,7 +86,7 @@ def test_noalloc_matches_regular_entry_points_on_two_calls_in_a_row():
 def test_noalloc_rejects_problems_beyond_its_scratch():
     import torch
     fn = _lib()
-    n, E = 1 << 22, 1 << 20  # 12 n + 104 E > 64 MiB
+    n, E = 1 << 22, 1 << 20  # 12 n + 216 E + 200 KiB > 64 MiB
     src = torch.zeros(E, dtype=torch.int32, device="cuda")
     out = torch.zeros(n, dtype=torch.int64, device="cuda")
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
