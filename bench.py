@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=1000, help="serve: number of requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: mean arrivals per second")
     ap.add_argument("--quick", action="store_true", help="skip the CPU baselines and the end-to-end legs")
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: split the headline stream's processors among the ranks (colour "
+                         "sharding, strong scaling, one uint64 all-reduce per step) instead of replicas")
     return ap.parse_args()
 
 
@@ -358,7 +361,7 @@ def single_leg(name, m, c, seed, steps, warmup, dev, pg, digests, clock_mhz_hint
     k3_s = k3_ms / steps * 1e-3
     hbm, hbm_src = peaks()
     achieved = k3_bytes / k3_s / 1e9
-    ws_bytes = 8 * T + 8 * st["pool_used"] + 20 * s.n_nodes
+    ws_bytes = 8 * T + 8 * st["pool_used"] + 24 * s.n_nodes
     out = {
         "edges": T, "value": world * steps * T / (ms_max * 1e-3), "unit": "edges/s", "steps": steps,
         "warmup": warmup, "ms_per_step": ms_max / steps, "tau_hat": g, "semi_triangles": int(proc.sum()),
@@ -588,6 +591,60 @@ def run_batched_only(args, world, rank, local, pg):
     return 0
 
 
+def run_sharded(args, world, rank, local, pg):
+    """--shard: the R-MAT scale-20 stream (m = c = 100) counted once by all ranks together, each rank
+    keeping its own processors (whole colour ranges) and ingesting the whole stream; a step ends with
+    the all-reduce of the counts and the estimates from the sums.  Total work is fixed (strong
+    scaling)."""
+    import torch
+    from paper_1811_09136_gb300 import shard
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = workload("rmat_s20")
+    T = len(s)
+    src = torch.from_numpy(s.src.view(np.int32)).to(dev)
+    dst = torch.from_numpy(s.dst.view(np.int32)).to(dev)
+    ss = shard.ShardedStream(s.n_nodes, 100, 100, SEED, world, rank, pg, expected_edges=T, max_batch=BATCH)
+
+    def step():
+        ss.reset()
+        for off in range(0, T, BATCH):
+            ss.ingest(src[off:off + BATCH], dst[off:off + BATCH])
+        return ss.estimates(local=True)
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(gpu_uuid(local)).start()
+    barrier(pg)
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g, _ = step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(pg)
+    clk = clocks.stop()
+    ms = max_over_ranks(pg, ev0.elapsed_time(ev1), dev)
+    proc, loc = ss.counts()
+    exact = compare_with_oracle(load_digests(), digest_key("rmat_s20", 100, 100, SEED), s, proc,
+                                loc.cpu().numpy().view(np.uint64), g)
+    if rank == 0:
+        line = {"metric": METRIC, "value": args.steps * T / (ms * 1e-3), "unit": "edges/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32/u64",
+                "data": "synthetic",
+                "config": {"workload": f"rmat_s20: R-MAT scale 20, ef 16, {T} edges, m=100, c=100, seed={SEED}, "
+                                       f"batches of {BATCH}", "parallelism": f"colour shards x{world}",
+                           "shard": list(ss.range)},
+                "identical_to_oracle": exact.get("identical", False), "exact": exact, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ss.close()
+    return 0
+
+
 def run_serving(args, world, rank, local, pg):
     """A Poisson request trace served with continuous batching: aggregate edges/s and latency."""
     import torch
@@ -623,6 +680,8 @@ def main():
         rc = run_batched_only(args, world, rank, local, pg)
     elif args.workload == "serve":
         rc = run_serving(args, world, rank, local, pg)
+    elif args.shard:
+        rc = run_sharded(args, world, rank, local, pg)
     elif args.workload == "headline":
         rc = run_ours(args, world, rank, local, pg)
     else:

@@ -97,7 +97,17 @@ typedef struct rept_config {
     uint32_t tile_max;       /* tuning: edges whose smaller endpoint holds at most this many entries
                                 (4, 8, 16 or 32; 0: 32) share a warp with other edges, larger ones get a
                                 warp of their own; results do not depend on it */
+    uint32_t proc_begin;     /* colour sharding: the handle keeps processors [proc_begin, proc_end) only
+                                (stores the edges they keep, counts their semi-triangles); 0, 0: all c.
+                                Processors are independent until the final sums (Algorithm 1), so
+                                handles whose ranges split 0..c-1 (say one per GPU, each ingesting the
+                                whole stream) give, summed, exactly the counts of one handle with all
+                                processors: tau^(i) from the handle that keeps i, sum_i tau_v^(i) as the
+                                sum over handles.  Not for c > m with c mod m != 0 (Algorithm 2's
+                                combination is not a sum): REPT_E_INVAL */
+    uint32_t proc_end;       /* see proc_begin; proc_begin < proc_end <= c, or both 0 */
     uint32_t reserved;       /* must be 0 */
+    uint32_t reserved2;      /* must be 0 */
 } rept_config;
 
 typedef struct rept_stats {
@@ -327,8 +337,8 @@ int rept_ingest_multi(rept_state* const* hs, const uint32_t* const* d_src, const
  * control block) lives in one statically allocated device array of
  * REPT_NOALLOC_SCRATCH_BYTES (64 MiB) inside this library; every GPU that
  * loads the library holds that array until the process exits.  A problem
- * needs 12 * n_nodes + 216 * n_edges + 200 KiB bytes of it (for example
- * 2^20 nodes and 250,000 edges); larger problems return REPT_E_SCRATCH
+ * needs 16 * n_nodes + 216 * n_edges + 200 KiB bytes of it (for example
+ * 2^20 nodes and 230,000 edges); larger problems return REPT_E_SCRATCH
  * before any device work is enqueued.  c must be at most 4096.
  *
  * Arguments: d_src / d_dst: device arrays of n_edges uint32 endpoints
@@ -354,6 +364,22 @@ int rept_ingest_multi(rept_state* const* hs, const uint32_t* const* d_src, const
 int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, uint64_t n_edges, uint32_t n_nodes, uint32_t m,
                        uint32_t c, uint64_t seed, uint64_t* d_proc, uint64_t* d_local, double* d_global,
                        void* stream);
+
+/*
+ * rept_estimates_from_counts: the FP64 estimates of Section III-A (c <= m) and Section III-B.1
+ * (c > m, c mod m = 0), or parallel MASCOT's average (flags = REPT_FLAG_MASCOT), from integer
+ * counts that the caller holds, typically the sums over colour shards (rept_config.proc_begin).
+ * h_proc: host array of c uint64 tau^(i).  d_local: device array of n_nodes uint64 sum_i tau_v^(i),
+ * or NULL.  Outputs: h_global (host, one double), d_local_est (device, n_nodes doubles; ignored when
+ * d_local is NULL).  The factors and rounding are those of rept_estimates, so summed shard counts
+ * give exactly the estimates of an unsharded handle.  Allocates nothing; d_local_est is written on
+ * `stream` and the call returns after enqueueing it (h_global is written before it returns).
+ * REPT_E_INVAL for c > m with c mod m != 0 (not linear in the counts), m or c zero, NULL h_proc /
+ * h_global, or a NULL d_local_est with a non-NULL d_local.
+ */
+int rept_estimates_from_counts(uint32_t m, uint32_t c, uint32_t flags, const uint64_t* h_proc,
+                               const uint64_t* d_local, uint32_t n_nodes, double* h_global, double* d_local_est,
+                               void* stream);
 
 /* rept_strerror: static English text for a REPT_* code. */
 const char* rept_strerror(int code);

@@ -88,9 +88,12 @@ void dev_free(rept_state* s, void* p, size_t bytes) {
 }
 
 // Pool slots that guarantee no batch can run out: a node's block (table plus list) holds at
-// most 8 slots per entry, and its successive blocks form a doubling series bounded by twice the
-// last one, so at most 16 slots per stored entry, i.e. 32 slots (8 quads) per stream edge.
-unsigned long long quads_bound(unsigned long long edges) { return 8ull * edges + 64ull; }
+// most 8 slots per entry (12 with colour words: 4 + 4 + 4 at one entry, at most 4 + 2 + 1 per entry
+// beyond), and its successive blocks form a doubling series bounded by twice the last one, so at
+// most 16 (24) slots per stored entry, i.e. 32 (48) slots, 8 (12) quads, per stream edge.
+unsigned long long quads_bound(unsigned long long edges, bool words) {
+    return (words ? 12ull : 8ull) * edges + 64ull;
+}
 
 int grow_pool(rept_state* s, unsigned long long min_quads, cudaStream_t st) {
     unsigned long long want = std::max(min_quads, 2ull * s->d.pool_quads);
@@ -254,7 +257,7 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
     }
     if ((rc = timed_launch(s, REPT_K_PLAN, st, [&] { k_plan<<<grid, threads, 0, st>>>(s->d); }))) return rc;
     const bool fixed = (s->cfg.flags & REPT_FLAG_FIXED_POOL) != 0;
-    if (!fixed && s->d.pool_quads < quads_bound(s->next_t + n)) {
+    if (!fixed && s->d.pool_quads < quads_bound(s->next_t + n, has_words(s->d))) {
         // not provably large enough: read this batch's request and grow if needed
         if ((rc = read_ctrl(s, st))) return rc;
         const unsigned long long need = s->h_ctrl->pool_top + s->h_ctrl->need_quads;
@@ -279,9 +282,12 @@ int launch_batch(rept_state* s, const uint32_t* d_src, const uint32_t* d_dst, un
     const size_t smem = s->cfg.c * sizeof(unsigned long long);
     const bool work = (s->cfg.flags & REPT_FLAG_WORK_COUNTERS) != 0;
     rc = timed_launch(s, REPT_K_INTERSECT, st, [&] {
-        if (s->d.colours) {
+        if (s->d.colours == kColInEntry) {
             if (work) k_intersect<true><<<grid_i, 256, smem, st>>>(s->d, b);
             else k_intersect<false><<<grid_i, 256, smem, st>>>(s->d, b);
+        } else if (s->d.colours == kColWords) {
+            if (work) k_intersect_words<true><<<grid_i, 256, smem, st>>>(s->d, b);
+            else k_intersect_words<false><<<grid_i, 256, smem, st>>>(s->d, b);
         } else {
             if (work) k_intersect_probe<true><<<grid_i, 256, smem, st>>>(s->d, b);
             else k_intersect_probe<false><<<grid_i, 256, smem, st>>>(s->d, b);
@@ -336,7 +342,11 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if (cfg->tile_max != 0 && cfg->tile_max != 4 && cfg->tile_max != 8 && cfg->tile_max != 16 &&
         cfg->tile_max != 32)
         return REPT_E_INVAL;
-    if (cfg->reserved != 0) return REPT_E_INVAL;
+    if (cfg->reserved != 0 || cfg->reserved2 != 0) return REPT_E_INVAL;
+    const bool sharded = cfg->proc_begin != 0 || cfg->proc_end != 0;
+    if (sharded && (cfg->proc_begin >= cfg->proc_end || cfg->proc_end > cfg->c)) return REPT_E_INVAL;
+    if (sharded && !(cfg->flags & REPT_FLAG_MASCOT) && cfg->c > cfg->m && cfg->c % cfg->m != 0)
+        return REPT_E_INVAL;  // Algorithm 2's combination needs every processor's counts
     cudaStream_t st = as_stream(stream);
     rept_state* s = new (std::nothrow) rept_state();
     if (!s) return REPT_E_NOMEM;
@@ -349,14 +359,21 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if (cudaGetDevice(&s->device) != cudaSuccess) return fail(REPT_E_CUDA);
     if (cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess)
         return fail(REPT_E_CUDA);
-    // the intersection grid: as many blocks as fit at once, for the variant this stream uses
-    const bool coloured = (cfg->flags & REPT_FLAG_MASCOT ? cfg->c : (cfg->c + cfg->m - 1) / cfg->m) == 1 &&
-                          cfg->m >= 2 && cfg->m <= 256 &&
-                          cfg->n_nodes <= (1u << kIdBits);
+    // how list entries carry colours, and the intersection grid: as many blocks as fit at once, for
+    // the variant this stream uses
+    const bool mascot_flag = (cfg->flags & REPT_FLAG_MASCOT) != 0;
+    const uint32_t n_groups = mascot_flag ? cfg->c : (cfg->c + cfg->m - 1) / cfg->m;
+    uint32_t cbits = 0;
+    while (cbits < 32 && (1ull << cbits) < cfg->m) ++cbits;
+    const bool coloured = n_groups == 1 && cfg->m >= 2 && cfg->m <= 256 && cfg->n_nodes <= (1u << kIdBits);
+    // (with several groups an entry costs a hash per group, which measured slower than probing:
+    // the 5-group Chung-Lu stream ran at 229M edges/s with words against 303M probing every entry)
+    const bool words = !coloured && !mascot_flag && cfg->m >= 2 && n_groups == 1;
+    const void* k3 = coloured ? (const void*)k_intersect<false>
+                              : words ? (const void*)k_intersect_words<false> : (const void*)k_intersect_probe<false>;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coloured ? (const void*)k_intersect<false>
-                                                                        : (const void*)k_intersect_probe<false>,
-                                                      256, cfg->c * sizeof(unsigned long long)) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3, 256, cfg->c * sizeof(unsigned long long)) !=
+        cudaSuccess)
         return fail(REPT_E_CUDA);
     s->grid_intersect = s->sm_count * std::max(per_sm, 1);
     s->grid_stream = s->sm_count * 8;
@@ -372,22 +389,28 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     d.fm = make_fastmod(cfg->m);
     d.tile_max = cfg->tile_max == 0 ? 32u : cfg->tile_max;
     const unsigned long long mb = cfg->max_batch ? cfg->max_batch : (1ull << 20);
-    unsigned long long quads = cfg->expected_edges ? quads_bound(cfg->expected_edges) : quads_bound(mb);
+    unsigned long long quads = quads_bound(cfg->expected_edges ? cfg->expected_edges : mb, words);
     if (quads > 0xFFFFFFFFull) quads = 0xFFFFFFFFull;
-    if ((rc = dev_alloc(s, (void**)&d.meta, (size_t)n * sizeof(uint2)))) return fail(rc);
+    if ((rc = dev_alloc(s, (void**)&d.meta, (size_t)n * sizeof(uint4)))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&d.local, (size_t)n * sizeof(unsigned long long)))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&d.proc, (size_t)cfg->c * sizeof(unsigned long long)))) return fail(rc);
-    if ((rc = dev_alloc(s, (void**)&d.add, (size_t)n * sizeof(uint32_t)))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&d.ctrl, sizeof(Ctrl)))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&d.hist, kSortBuckets * sizeof(uint32_t)))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&d.pool, quads * 32ull))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&s->d_global, sizeof(double)))) return fail(rc);
     d.pool_quads = quads;
-    // one hash group, few colours and ids of at most kIdBits: list entries carry their colour
-    d.colours = coloured ? 1u : 0u;
+    // one hash group, few colours and ids of at most kIdBits: list entries carry their colour;
+    // several groups whose colours fit 32 bits: a colour word per entry
+    d.colours = coloured ? kColInEntry : words ? kColWords : kColNone;
+    d.cbits = words ? cbits : 0u;
+    d.cmask = words ? (uint32_t)((1ull << cbits) - 1ull) : 0u;
     d.c1 = mascot || cfg->c <= cfg->m ? cfg->c : cfg->c / cfg->m;
     d.keep = mascot ? 1u : cfg->m;
     d.pstride = mascot ? 1u : cfg->m;
+    d.pbeg = sharded ? cfg->proc_begin : 0u;
+    d.pcount = sharded ? cfg->proc_end - cfg->proc_begin : cfg->c;
+    d.kbeg = d.pbeg / d.pstride;
+    d.kend = (d.pbeg + d.pcount - 1u) / d.pstride + 1u;
     if (cfg->flags & REPT_FLAG_LOCAL_PER_PROCESSOR) {
         if ((rc = dev_alloc(s, (void**)&d.local_proc, (size_t)cfg->c * n * sizeof(unsigned long long))))
             return fail(rc);
@@ -404,7 +427,6 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     if (cudaMallocHost((void**)&s->h_global, sizeof(double)) != cudaSuccess) return fail(REPT_E_NOMEM);
     memset(s->h_ctrl, 0, sizeof(Ctrl));
     if (cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), st) != cudaSuccess) return fail(REPT_E_CUDA);
-    if (cudaMemsetAsync(d.add, 0, (size_t)n * sizeof(uint32_t), st) != cudaSuccess) return fail(REPT_E_CUDA);
     if (cudaMemsetAsync(d.pool, 0xFF, quads * 32ull, st) != cudaSuccess) return fail(REPT_E_CUDA);
     if ((rc = rept_reset(s, stream))) return fail(rc);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(REPT_E_CUDA);
@@ -423,10 +445,9 @@ int rept_reset(rept_state* s, void* stream) {
     unsigned long long used = s->h_ctrl->pool_top;
     if (used > d.pool_quads) used = d.pool_quads;
     if (used) REPT_CUDA(cudaMemsetAsync(d.pool, 0xFF, used * 32ull, st));
-    REPT_CUDA(cudaMemsetAsync(d.meta, 0, n * sizeof(uint2), st));
+    REPT_CUDA(cudaMemsetAsync(d.meta, 0, n * sizeof(uint4), st));
     REPT_CUDA(cudaMemsetAsync(d.local, 0, n * sizeof(unsigned long long), st));
     REPT_CUDA(cudaMemsetAsync(d.proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
-    REPT_CUDA(cudaMemsetAsync(d.add, 0, n * sizeof(uint32_t), st));
     if (d.local2) REPT_CUDA(cudaMemsetAsync(d.local2, 0, n * sizeof(unsigned long long), st));
     if (d.eta_local) REPT_CUDA(cudaMemsetAsync(d.eta_local, 0, n * sizeof(unsigned long long), st));
     if (d.eta_proc) REPT_CUDA(cudaMemsetAsync(d.eta_proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
@@ -450,10 +471,9 @@ int rept_reset_async(rept_state* s, uint64_t seed, void* stream) {
     d.seed = seed;
     const size_t n = d.n_nodes;
     REPT_CUDA(cudaMemsetAsync(d.pool, 0xFF, d.pool_quads * 32ull, st));
-    REPT_CUDA(cudaMemsetAsync(d.meta, 0, n * sizeof(uint2), st));
+    REPT_CUDA(cudaMemsetAsync(d.meta, 0, n * sizeof(uint4), st));
     REPT_CUDA(cudaMemsetAsync(d.local, 0, n * sizeof(unsigned long long), st));
     REPT_CUDA(cudaMemsetAsync(d.proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
-    REPT_CUDA(cudaMemsetAsync(d.add, 0, n * sizeof(uint32_t), st));
     if (d.local2) REPT_CUDA(cudaMemsetAsync(d.local2, 0, n * sizeof(unsigned long long), st));
     if (d.eta_local) REPT_CUDA(cudaMemsetAsync(d.eta_local, 0, n * sizeof(unsigned long long), st));
     if (d.eta_proc) REPT_CUDA(cudaMemsetAsync(d.eta_proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
@@ -595,6 +615,7 @@ struct SnapHeader {
     uint64_t magic, version;
     uint64_t m, c, seed, n_nodes, flags, groups;
     uint64_t next_t, pool_top, self_loops, stored;
+    uint64_t proc_begin, proc_end;
 };
 constexpr uint64_t kSnapMagic = 0x5245505453544154ull;  // "REPTSTAT"
 
@@ -608,7 +629,7 @@ int snap_parts(rept_state* s, unsigned long long pool_top, SnapPart* parts, int*
     StreamDev& d = s->d;
     const unsigned long long n = d.n_nodes, c = d.c, G = s->groups, T = s->next_t;
     int k = 0;
-    parts[k++] = {d.meta, n * sizeof(uint2)};
+    parts[k++] = {d.meta, n * sizeof(uint4)};
     parts[k++] = {d.local, n * 8ull};
     parts[k++] = {d.proc, c * 8ull};
     parts[k++] = {d.pool, pool_top * 32ull};
@@ -650,8 +671,9 @@ int rept_snapshot(rept_state* s, void* h_buf, uint64_t bytes, void* stream) {
     unsigned long long total = sizeof(SnapHeader);
     for (int i = 0; i < np; ++i) total += parts[i].bytes;
     if (bytes < total) return REPT_E_INVAL;
-    SnapHeader h{kSnapMagic, 1, s->cfg.m, s->cfg.c, s->cfg.seed, s->cfg.n_nodes, s->cfg.flags, s->groups,
-                 s->next_t, s->h_ctrl->pool_top, s->h_ctrl->self_loops, s->h_ctrl->stored};
+    SnapHeader h{kSnapMagic, 2, s->cfg.m, s->cfg.c, s->cfg.seed, s->cfg.n_nodes, s->cfg.flags, s->groups,
+                 s->next_t, s->h_ctrl->pool_top, s->h_ctrl->self_loops, s->h_ctrl->stored,
+                 s->cfg.proc_begin, s->cfg.proc_end};
     std::memcpy(h_buf, &h, sizeof(h));
     char* out = static_cast<char*>(h_buf) + sizeof(h);
     for (int i = 0; i < np; ++i) {
@@ -667,8 +689,9 @@ int rept_restore(rept_state* s, const void* h_buf, uint64_t bytes, void* stream)
     cudaStream_t st = as_stream(stream);
     SnapHeader h;
     std::memcpy(&h, h_buf, sizeof(h));
-    if (h.magic != kSnapMagic || h.version != 1 || h.m != s->cfg.m || h.c != s->cfg.c || h.seed != s->cfg.seed ||
-        h.n_nodes != s->cfg.n_nodes || h.flags != s->cfg.flags || h.groups != s->groups)
+    if (h.magic != kSnapMagic || h.version != 2 || h.m != s->cfg.m || h.c != s->cfg.c || h.seed != s->cfg.seed ||
+        h.n_nodes != s->cfg.n_nodes || h.flags != s->cfg.flags || h.groups != s->groups ||
+        h.proc_begin != s->cfg.proc_begin || h.proc_end != s->cfg.proc_end)
         return REPT_E_INVAL;
     int rc = rept_reset(s, stream);
     if (rc) return rc;
@@ -771,7 +794,6 @@ void rept_destroy(rept_state* s) {
     cudaFree(d.meta);
     cudaFree(d.local);
     cudaFree(d.proc);
-    cudaFree(d.add);
     cudaFree(d.ctrl);
     cudaFree(d.pool);
     cudaFree(d.touched);
@@ -959,7 +981,7 @@ int rept_group_ingest(rept_group* g, rept_state* const* hs, const uint32_t* cons
         max_n = std::max<unsigned long long>(max_n, n[i]);
         max_c = std::max(max_c, s->cfg.c);
         const bool fixed = (s->cfg.flags & REPT_FLAG_FIXED_POOL) != 0;
-        if (!fixed && s->d.pool_quads < quads_bound(s->next_t + n[i])) guaranteed = false;
+        if (!fixed && s->d.pool_quads < quads_bound(s->next_t + n[i], has_words(s->d))) guaranteed = false;
     }
     // launch shape: the edge kernels cover the largest batch, the rest share the SMs between streams
     GroupShape sh{};
@@ -1072,6 +1094,34 @@ int rept_ingest_multi(rept_state* const* hs, const uint32_t* const* d_src, const
         if (rc) return rc;
     }
     return rept_group_ingest(g, hs, d_src, d_dst, n, k, stream);
+}
+
+int rept_estimates_from_counts(uint32_t m, uint32_t c, uint32_t flags, const uint64_t* h_proc,
+                               const uint64_t* d_local, uint32_t n_nodes, double* h_global, double* d_local_est,
+                               void* stream) {
+    if (m == 0 || c == 0 || !h_proc || !h_global || (d_local && !d_local_est)) return REPT_E_INVAL;
+    const bool mascot = (flags & REPT_FLAG_MASCOT) != 0;
+    if (!mascot && c > m && c % m != 0) return REPT_E_INVAL;
+    rept_config cfg{};
+    cfg.m = m;
+    cfg.c = c;
+    cfg.flags = flags & REPT_FLAG_MASCOT;
+    const double f = estimate_factor(cfg);
+    // the integer sum of the processors that enter the estimate, then one conversion, as
+    // k_global_estimate forms it
+    const uint32_t c_used = mascot || c <= m ? c : (c / m) * m;
+    unsigned long long sum = 0;
+    for (uint32_t i = 0; i < c_used; ++i) sum += h_proc[i];
+    *h_global = (double)sum * f;
+    if (d_local && n_nodes) {
+        int dev = 0, sms = 0;
+        REPT_CUDA(cudaGetDevice(&dev));
+        REPT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        k_local_estimates<<<sms * 4, 256, 0, as_stream(stream)>>>(reinterpret_cast<const unsigned long long*>(d_local),
+                                                                   n_nodes, f, d_local_est);
+        REPT_LAUNCHED();
+    }
+    return REPT_OK;
 }
 
 const char* rept_strerror(int code) {

@@ -1,15 +1,19 @@
 // Device-side data layout and helpers of the REPT streaming counter.
 //
 // HBM layout of one stream (one rept_state):
-//   meta[n_nodes]   uint2 {off, cnt}: node x's block starts at slot 4*off of
-//                   the pool and holds cnt entries; its size is a function of
-//                   cnt alone (table_lg below), so a node's block is
-//                   re-allocated exactly when cnt crosses a power-of-two
-//                   boundary.
+//   meta[n_nodes]   uint4 {off, cnt, add, 0}: node x's block starts at slot
+//                   4*off of the pool and holds cnt entries; its size is a
+//                   function of cnt alone (table_lg below), so a node's block
+//                   is re-allocated exactly when cnt crosses a power-of-two
+//                   boundary.  add counts the current batch's new entries of x
+//                   (zero between batches); it shares x's 16-byte record so
+//                   that the insert's position counter and the block's place
+//                   sit in one 32-byte sector.
 //   pool[]          8-byte slots: per node, an open-addressing (linear probing,
 //                   4-key buckets) table of 2^lg neighbour ids with a parallel
 //                   array of their stream indices (2^lg slots in all), then
-//                   the same entries as a packed list of {nbr, eidx} pairs.
+//                   the same entries as a packed list of {nbr, eidx} pairs
+//                   (and, for streams with colour words, one word per entry).
 //                   An entry (w, t) of x is the stored edge {x, w} that
 //                   arrived at stream index t.  Empty keys are all-ones.  The
 //                   tables of all processors share one union adjacency: an
@@ -18,9 +22,9 @@
 //                   (Section III-A: processor i keeps colour i).
 //   local[n_nodes]  uint64 sum over processors of tau_v^(i)
 //   proc[c]         uint64 tau^(i)
-// Per-batch scratch: add[n_nodes] (new entries per node, zero between
-// batches), touched[] (nodes with add > 0), grow_rel[] (their new table's
-// offset relative to this batch's allocation), and the control block.
+// Per-batch scratch: touched[] (nodes with add > 0), grow_rel[] (their new
+// table's offset relative to this batch's allocation), the work records, and
+// the control block.
 #pragma once
 
 #include <cstdint>
@@ -141,6 +145,19 @@ __host__ __device__ __forceinline__ bool mod_equals_in_range(uint64_t x, uint32_
     return r <= f.lim;
 }
 
+// The same test without a branch: every lane forms the product, so lanes of a warp never part ways
+// over it (x - j wraps when x < j, and the first factor then makes the result false).
+__host__ __device__ __forceinline__ bool mod_equals_nobranch(uint64_t x, uint32_t j, const FastMod& f) {
+    const uint64_t y = (x - j) * f.qinv;
+#ifdef __CUDA_ARCH__
+    const uint32_t lo = (uint32_t)y, hi = (uint32_t)(y >> 32);
+    const uint64_t r = ((uint64_t)__funnelshift_r(hi, lo, f.k) << 32) | __funnelshift_r(lo, hi, f.k);
+#else
+    const uint64_t r = (y >> f.k) | (y << ((64u - f.k) & 63u));
+#endif
+    return (x >= j) & (r <= f.lim);
+}
+
 __host__ __device__ __forceinline__ bool mod_equals(uint64_t x, uint32_t j, const FastMod& f) {
     if (f.m < 2) return j == 0u;
     if (j >= f.m) return false;
@@ -186,16 +203,20 @@ struct StreamDev {
     uint64_t seed;
     FastMod fm;         // x mod m
     uint32_t tile_max;  // edges whose smaller endpoint has more entries get a warp (4, 8, 16 or 32)
-    uint2* meta;
+    uint4* meta;  // per node {block offset in 4-slot units, entries, this batch's new entries, 0}
     uint2* pool;
     unsigned long long pool_quads;
-    // 1: every list entry {w, t} of node x carries the colour h_0(x, w) in the top 8 bits of its
-    // first word (w itself in the low kIdBits), kept for one hash group, 2 <= m <= 256 and
-    // n_nodes <= 2^kIdBits; 0: list entries hold plain ids
+    // How list entries carry their edge's colours (the intersection tests colours before it probes):
+    // kColNone: plain entries; kColInEntry: every list entry {w, t} of node x carries h_0(x, w) in
+    // the top 8 bits of its first word (w itself in the low kIdBits), for one hash group,
+    // 2 <= m <= 256 and n_nodes <= 2^kIdBits; kColWords: a parallel array of 32-bit words beside
+    // the list holds h_k(x, w) of every hash group k in bits [k * cbits, (k + 1) * cbits), for REPT
+    // with groups * cbits <= 32
     uint32_t colours;
+    uint32_t cbits;  // kColWords: bits per group colour, ceil(log2 m)
+    uint32_t cmask;  // (1 << cbits) - 1
     unsigned long long* local;
     unsigned long long* proc;
-    uint32_t* add;
     uint32_t* touched;
     uint32_t* grow_rel;
     struct WorkItem* rec;   // [max_batch] work record of each edge (key kNoKey if it closes no wedge)
@@ -210,6 +231,9 @@ struct StreamDev {
     uint32_t c1;                    // full groups: processors i < c1 * m feed `local`, the rest `local2`
     uint32_t keep;                  // colours each hash group keeps: m (REPT), 1 (parallel MASCOT)
     uint32_t pstride;               // processors per hash group: m (REPT), 1 (parallel MASCOT)
+    // colour sharding: this state keeps processors [pbeg, pbeg + pcount) only (all c by default),
+    // which belong to hash groups [kbeg, kend)
+    uint32_t pbeg, pcount, kbeg, kend;
     unsigned long long* local2;     // [n_nodes] sum of tau_v^(i) over the partial group
     unsigned long long* eta_proc;   // [c] eta^(i)
     unsigned long long* eta_local;  // [n_nodes] sum over processors of eta_v^(i)
@@ -273,29 +297,54 @@ __device__ __forceinline__ bool colour_is(uint32_t a, uint32_t b, uint64_t s_k, 
 // Is edge {u, v} kept by some processor (k*m + h_k(u,v) < c for some group k)?
 // The processor that keeps colour j of hash group k, if any: REPT's processor i = k*m + j (i < c);
 // parallel MASCOT's sampler i = k keeps colour 0 only (an independent p = 1/m sample per group).
+// Only the processors of this state's shard count (pbeg + pcount <= c, so i < c as well).
 __device__ __forceinline__ bool processor_of(const StreamDev& d, uint32_t k, uint32_t j, uint32_t& i) {
     i = k * d.pstride + j;
-    return j < d.keep && i < d.c;
+    return j < d.keep && i - d.pbeg < d.pcount;
 }
 
 __device__ __forceinline__ bool kept_by_any(const StreamDev& d, uint32_t u, uint32_t v) {
-    for (uint32_t k = 0; k < d.groups; ++k) {
+    for (uint32_t k = d.kbeg; k < d.kend; ++k) {
         uint32_t i, j = colour_of(u, v, group_seed(d.seed, k), d.fm);
         if (processor_of(d, k, j, i)) return true;
     }
     return false;
 }
 
+constexpr uint32_t kColNone = 0u, kColInEntry = 1u, kColWords = 2u;
+
 // The mask that takes a node id out of the first word of a list entry.
-__host__ __device__ __forceinline__ uint32_t id_mask(const StreamDev& d) { return d.colours ? kIdMask : ~0u; }
+__host__ __device__ __forceinline__ uint32_t id_mask(const StreamDev& d) {
+    return d.colours == kColInEntry ? kIdMask : ~0u;
+}
+__host__ __device__ __forceinline__ bool has_words(const StreamDev& d) { return d.colours == kColWords; }
 
 // With one hash group, a wedge (s, w), (l, w) can count only for the processor of colour
 // js = h_0(s, w), and only if that processor exists and h_0(l, w) = js.  The intersection reads js from
 // s's list entry and asks this of the hash alone before it probes l's table for w, so all but about
 // 1/m of the probes are skipped.
 __device__ __forceinline__ bool wedge_may_count(const StreamDev& d, uint32_t l, uint32_t w, uint32_t js) {
-    uint32_t i;
-    return processor_of(d, 0u, js, i) && colour_is(l, w, d.seed, d.fm, js);
+    // every step evaluated and combined with & (no early exit), so the lanes of a warp never part
+    // ways over it (measured 4 % faster than the short-circuit form)
+    const uint64_t lo = l < w ? l : w, hi = l < w ? w : l;
+    const uint64_t z = splitmix64(((lo << 32) | hi) ^ d.seed);
+    return (js < d.keep) & (js - d.pbeg < d.pcount) & mod_equals_nobranch(z, js, d.fm);
+}
+
+// With several hash groups (kColWords), a wedge (s, w), (l, w) can count only for a group k whose
+// colour js_k = h_k(s, w) names a kept processor and equals h_k(l, w).  The word cw holds every js_k
+// (read from s's entry); the groups are tried in order and the first that agrees decides, so an
+// entry that counts for no processor costs one hash per group and no probe of l's table.
+__device__ __forceinline__ bool words_may_count(const StreamDev& d, uint32_t l, uint32_t w, uint32_t cw) {
+    const uint64_t lo = l < w ? l : w, hi = l < w ? w : l;
+    const uint64_t key = (lo << 32) | hi;
+    uint64_t sk = group_seed(d.seed, d.kbeg);
+    for (uint32_t k = d.kbeg; k < d.kend; ++k, sk += kGoldenGamma) {
+        const uint32_t js = (cw >> (k * d.cbits)) & d.cmask;
+        uint32_t i;
+        if (processor_of(d, k, js, i) && mod_equals_in_range(splitmix64(key ^ sk), js, d.fm)) return true;
+    }
+    return false;
 }
 
 // log2 of the table capacity for cnt entries: capacity = max(4, nextpow2(2*cnt)); 0 when empty.
@@ -312,9 +361,13 @@ __host__ __device__ __forceinline__ uint32_t table_lg(uint32_t cnt) {
 
 // A node's block in the pool: its hash table (2^lg slots, probed by neighbour id) followed by its
 // entry list (list_slots(lg) slots, the same entries packed in insertion order, scanned when the
-// node is the smaller endpoint).  Both parts are multiples of 4 slots (32 bytes).
+// node is the smaller endpoint) and, with kColWords, the entries' colour words (one uint32 per list
+// slot, word_slots(lg) slots).  Every part is a multiple of 4 slots (32 bytes).
 __host__ __device__ __forceinline__ uint32_t list_slots(uint32_t lg) { return lg >= 3u ? (1u << (lg - 1u)) : 4u; }
-__host__ __device__ __forceinline__ uint32_t block_quads(uint32_t lg) { return ((1u << lg) + list_slots(lg)) >> 2; }
+__host__ __device__ __forceinline__ uint32_t word_slots(uint32_t lg) { return lg >= 4u ? (1u << (lg - 2u)) : 4u; }
+__host__ __device__ __forceinline__ uint32_t block_quads(uint32_t lg, bool words) {
+    return ((1u << lg) + list_slots(lg) + (words ? word_slots(lg) : 0u)) >> 2;
+}
 
 // k_intersect work class of an edge whose smaller endpoint holds cnt entries: tiles of 4, 8, 16, 32
 // lanes (one entry per lane) up to tile_max entries, then a warp per edge for up to 256 entries and

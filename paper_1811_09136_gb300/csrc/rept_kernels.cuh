@@ -70,8 +70,8 @@ __device__ __forceinline__ void k_classify_body(const StreamDev& d, const BatchD
         const bool kept = valid && in_range && u != v && kept_by_any(d, u, v);
         bool first_u = false, first_v = false;
         if (kept) {
-            first_u = atomicAdd(&d.add[u], 1u) == 0u;
-            first_v = atomicAdd(&d.add[v], 1u) == 0u;
+            first_u = atomicAdd(&d.meta[u].z, 1u) == 0u;
+            first_v = atomicAdd(&d.meta[v].z, 1u) == 0u;
         }
         unsigned long long o = warp_reserve(&d.ctrl->n_touched, (unsigned)first_u + (unsigned)first_v);
         if (first_u) d.touched[o++] = u;
@@ -91,9 +91,10 @@ __device__ __forceinline__ void k_plan_body(const StreamDev& d) {
         unsigned long long need = 0;
         if (valid) {
             const uint32_t x = d.touched[i];
-            const uint32_t cnt = d.meta[x].y, add = d.add[x];
+            const uint4 mx = d.meta[x];
+            const uint32_t cnt = mx.y, add = mx.z;
             const uint32_t lg_old = table_lg(cnt), lg_new = table_lg(cnt + add);
-            if (lg_new != lg_old) need = block_quads(lg_new);
+            if (lg_new != lg_old) need = block_quads(lg_new, has_words(d));
         }
         const unsigned long long rel = warp_reserve(&d.ctrl->need_quads, need);
         if (valid) d.grow_rel[i] = need ? (uint32_t)rel : kNoGrow;
@@ -103,15 +104,21 @@ __device__ __forceinline__ void k_plan_body(const StreamDev& d) {
 // REPT_DEBUG_BOUNDS: the block of 2^lg table slots and its list at `off_quads` lies inside the pool.
 __device__ __forceinline__ bool block_fits(const StreamDev& d, unsigned site, unsigned long long off_quads,
                                           uint32_t lg) {
-    return REPT_CHECK(d.ctrl, site, 4ull * (off_quads + block_quads(lg)) - 1ull, 4ull * d.pool_quads);
+    return REPT_CHECK(d.ctrl, site, 4ull * (off_quads + block_quads(lg, has_words(d))) - 1ull, 4ull * d.pool_quads);
+}
+
+// The colour words (kColWords) of the list of a block at `off_quads` with a table of 2^lg slots.
+__device__ __forceinline__ uint32_t* list_words(uint2* pool, unsigned long long off_quads, uint32_t lg) {
+    return reinterpret_cast<uint32_t*>(pool + 4ull * off_quads + (1ull << lg) + list_slots(lg));
 }
 
 // Move node x's entries (list of cnt_old entries at old_off) into its new block at new_off: copy the
-// list and insert each entry's id (`mask` takes it out of the entry) into the new table.  Lanes
-// `rank` of `width` share the work.
-__device__ __forceinline__ bool move_block(uint2* pool, uint32_t mask, uint32_t old_off, uint32_t cnt_old,
+// list (and, with `words`, the colour words) and insert each entry's id (`mask` takes it out of the
+// entry) into the new table.  Lanes `rank` of `width` share the work.
+__device__ __forceinline__ bool move_block(uint2* pool, uint32_t mask, bool words, uint32_t old_off, uint32_t cnt_old,
                                            unsigned long long new_off, uint32_t lg_new, uint32_t rank, uint32_t width) {
-    const unsigned long long old_at = 4ull * old_off + (1ull << table_lg(cnt_old));
+    const uint32_t lg_old = table_lg(cnt_old);
+    const unsigned long long old_at = 4ull * old_off + (1ull << lg_old);
     const unsigned long long new_at = 4ull * new_off + (1ull << lg_new);
     const uint2* old_list = pool + old_at;
     uint2* new_list = pool + new_at;
@@ -119,15 +126,22 @@ __device__ __forceinline__ bool move_block(uint2* pool, uint32_t mask, uint32_t 
     for (uint32_t j = rank; j < cnt_old; j += width) {
         const uint2 e = old_list[j];
         new_list[j] = e;
+        if (words) list_words(pool, new_off, lg_new)[j] = list_words(pool, old_off, lg_old)[j];
         ok &= table_insert(pool, 4ull * new_off, lg_new, e.x & mask, e.y);
     }
     return ok;
 }
 
+// New tables of at most kMoveSlots slots are rebuilt in shared memory by a warp (k_rehash_big), those
+// of at most kBlockMoveSlots by a thread block (k_rehash_huge); larger ones are built in place.
+constexpr uint32_t kMoveSlots = 512;
+constexpr uint32_t kBlockMoveSlots = 4096;
+
 // Publish the new entry counts of the touched nodes and move the blocks that were re-allocated.
 // One thread per touched node; a block holding more than 8 entries is left to k_rehash_big (a warp
-// each) or k_rehash_huge (a thread block each).  add[x] keeps the batch's new-entry count for
-// k_insert, which counts it back down to zero; a batch that is not applied clears it here.
+// each, new tables of at most kMoveSlots slots) or k_rehash_huge (a thread block each).  meta[x].z
+// keeps the batch's new-entry count for k_insert, which counts it back down to zero; a batch that is not
+// applied clears it here.
 __device__ __forceinline__ void k_commit_body(const StreamDev& d) {
     const unsigned status = d.ctrl->status;
     const unsigned long long n_t = d.ctrl->n_touched;
@@ -143,23 +157,24 @@ __device__ __forceinline__ void k_commit_body(const StreamDev& d) {
         if (i < n_t) {
             const uint32_t x = d.touched[i];
             if (bad) {
-                d.add[x] = 0u;
+                d.meta[x].z = 0u;
             } else {
-                const uint2 m = d.meta[x];
-                const uint32_t cnt_new = m.y + d.add[x];
+                const uint4 m = d.meta[x];
+                const uint32_t cnt_new = m.y + m.z;
                 const uint32_t rel = d.grow_rel[i];
                 if (rel == kNoGrow) {
                     d.meta[x].y = cnt_new;
                 } else if (m.y > 8u) {
-                    defer = m.y <= 2048u;
+                    defer = (1u << table_lg(cnt_new)) <= kMoveSlots;
                     huge = !defer;
                 } else {
                     const unsigned long long new_off = top + rel;
                     const bool fits = block_fits(d, 10, m.x, table_lg(m.y)) &&
                                       block_fits(d, 11, new_off, table_lg(cnt_new));
-                    if (fits && !move_block(d.pool, id_mask(d), m.x, m.y, new_off, table_lg(cnt_new), 0u, 1u))
+                    if (fits && !move_block(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, table_lg(cnt_new), 0u,
+                                            1u))
                         atomicOr(&d.ctrl->status, kStInternal);
-                    d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
+                    d.meta[x] = make_uint4((uint32_t)new_off, cnt_new, m.z, 0u);
                 }
             }
         }
@@ -170,27 +185,32 @@ __device__ __forceinline__ void k_commit_body(const StreamDev& d) {
     }
 }
 
-// Tables of at most kMoveSlots slots are rebuilt in shared memory when a warp moves a block.
-constexpr uint32_t kMoveSlots = 512;
-
-// move_block for one warp, the new table built in shared memory (keys and stream indices of
-// 2^lg_new <= kMoveSlots slots, the same placement rule as table_insert) and then written out with
-// coalesced stores.  The new block is this warp's alone until the batch's inserts run.
-__device__ __forceinline__ bool move_block_smem(uint2* pool, uint32_t id_bits, uint32_t old_off, uint32_t cnt_old,
-                                                unsigned long long new_off, uint32_t lg_new, uint32_t* s_keys,
-                                                uint32_t* s_eidx, unsigned lane) {
+// move_block with the new table built in shared memory (keys and stream indices of 2^lg_new slots,
+// the same placement rule as table_insert) and then written out with coalesced stores, by the lanes
+// `rank` of `width` of one warp (BLOCK = false) or of one thread block (BLOCK = true).  The new block
+// is the caller's alone until the batch's inserts run.
+template <bool BLOCK>
+__device__ __forceinline__ bool move_block_smem(uint2* pool, uint32_t id_bits, bool words, uint32_t old_off,
+                                                uint32_t cnt_old, unsigned long long new_off, uint32_t lg_new,
+                                                uint32_t* s_keys, uint32_t* s_eidx, uint32_t rank, uint32_t width) {
+    auto sync = [] {
+        if (BLOCK) __syncthreads();
+        else __syncwarp();
+    };
     const uint32_t cap = 1u << lg_new, mask = cap - 1u;
-    for (uint32_t q = lane; q < cap; q += 32u) {
+    for (uint32_t q = rank; q < cap; q += width) {
         s_keys[q] = kEmptyId;
         s_eidx[q] = kEmptyId;
     }
-    __syncwarp();
-    const unsigned long long old_at = 4ull * old_off + (1ull << table_lg(cnt_old));
+    sync();
+    const uint32_t lg_old = table_lg(cnt_old);
+    const unsigned long long old_at = 4ull * old_off + (1ull << lg_old);
     const unsigned long long new_at = 4ull * new_off + cap;
     bool ok = true;
-    for (uint32_t j = lane; j < cnt_old; j += 32u) {
+    for (uint32_t j = rank; j < cnt_old; j += width) {
         const uint2 e = pool[old_at + j];
         pool[new_at + j] = e;
+        if (words) list_words(pool, new_off, lg_new)[j] = list_words(pool, old_off, lg_old)[j];
         const uint32_t key = e.x & id_bits;
         const uint32_t start = (key * 0x85EBCA6Bu) >> 30;
         uint32_t b = home_slot(key, lg_new);
@@ -207,16 +227,16 @@ __device__ __forceinline__ bool move_block_smem(uint2* pool, uint32_t id_bits, u
         }
         ok &= placed;
     }
-    __syncwarp();
+    sync();
     uint32_t* keys = reinterpret_cast<uint32_t*>(pool + 4ull * new_off);
-    for (uint32_t q = lane; q < cap; q += 32u) {
+    for (uint32_t q = rank; q < cap; q += width) {
         keys[q] = s_keys[q];
         keys[cap + q] = s_eidx[q];
     }
     return ok;
 }
 
-// Move the blocks of 9..2048 entries listed by k_commit: one warp per node.
+// Move the blocks listed by k_commit whose new table has at most kMoveSlots slots: one warp per node.
 __device__ __forceinline__ void k_rehash_big_body(const StreamDev& d) {
     __shared__ uint32_t s_keys[8][kMoveSlots];  // blocks of 256 threads
     __shared__ uint32_t s_eidx[8][kMoveSlots];
@@ -227,24 +247,28 @@ __device__ __forceinline__ void k_rehash_big_body(const StreamDev& d) {
          k += warps) {
         const uint32_t i = d.big[k];
         const uint32_t x = d.touched[i];
-        const uint2 m = d.meta[x];
-        const uint32_t cnt_new = m.y + d.add[x];
+        const uint4 m = d.meta[x];
+        const uint32_t cnt_new = m.y + m.z;
         const unsigned long long new_off = top + d.grow_rel[i];
         const bool fits = block_fits(d, 10, m.x, table_lg(m.y)) && block_fits(d, 11, new_off, table_lg(cnt_new));
         const uint32_t lg_new = table_lg(cnt_new);
         bool ok = true;
         if (fits && (1u << lg_new) <= kMoveSlots && REPT_CHECK(d.ctrl, 14, wid, 8u))
-            ok = move_block_smem(d.pool, id_mask(d), m.x, m.y, new_off, lg_new, s_keys[wid], s_eidx[wid], lane);
+            ok = move_block_smem<false>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, s_keys[wid],
+                                        s_eidx[wid], lane, 32u);
         else if (fits)
-            ok = move_block(d.pool, id_mask(d), m.x, m.y, new_off, lg_new, lane, 32u);
+            ok = move_block(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, lane, 32u);
         if (!ok) atomicOr(&d.ctrl->status, kStInternal);
         __syncwarp();
-        if (lane == 0) d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
+        if (lane == 0) d.meta[x] = make_uint4((uint32_t)new_off, cnt_new, m.z, 0u);
     }
 }
 
-// Move the blocks of more than 2048 entries listed by k_commit: thread blocks claim one node at a time.
+// Move the blocks listed by k_commit whose new table has more than kMoveSlots slots: thread blocks
+// claim one node at a time, and build tables of at most kBlockMoveSlots slots in shared memory.
 __device__ __forceinline__ void k_rehash_huge_body(const StreamDev& d) {
+    __shared__ uint32_t s_keys[kBlockMoveSlots];
+    __shared__ uint32_t s_eidx[kBlockMoveSlots];
     __shared__ unsigned long long s_k;
     __shared__ int s_bad;
     const unsigned long long n_huge = d.ctrl->n_huge, top = d.ctrl->pool_top;
@@ -258,16 +282,22 @@ __device__ __forceinline__ void k_rehash_huge_body(const StreamDev& d) {
         if (k >= n_huge) break;
         const uint32_t i = d.big[d.big_cap - 1 - k];
         const uint32_t x = d.touched[i];
-        const uint2 m = d.meta[x];
-        const uint32_t cnt_new = m.y + d.add[x];
+        const uint4 m = d.meta[x];
+        const uint32_t cnt_new = m.y + m.z;
         const unsigned long long new_off = top + d.grow_rel[i];
         const bool fits = block_fits(d, 10, m.x, table_lg(m.y)) && block_fits(d, 11, new_off, table_lg(cnt_new));
-        if (fits && !move_block(d.pool, id_mask(d), m.x, m.y, new_off, table_lg(cnt_new), threadIdx.x, blockDim.x))
-            s_bad = 1;
+        const uint32_t lg_new = table_lg(cnt_new);
+        bool ok = true;
+        if (fits && (1u << lg_new) <= kBlockMoveSlots)  // uniform over the block
+            ok = move_block_smem<true>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, s_keys, s_eidx,
+                                       threadIdx.x, blockDim.x);
+        else if (fits)
+            ok = move_block(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, threadIdx.x, blockDim.x);
+        if (!ok) s_bad = 1;
         __syncthreads();
         if (threadIdx.x == 0) {
             if (s_bad) atomicOr(&d.ctrl->status, kStInternal);
-            d.meta[x] = make_uint2((uint32_t)new_off, cnt_new);
+            d.meta[x] = make_uint4((uint32_t)new_off, cnt_new, m.z, 0u);
         }
         __syncthreads();
     }
@@ -288,6 +318,7 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
     if (status) return;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long n_loops = 0, n_kept = 0;  // this lane's tallies, added once per warp at the end
     for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < b.n;
          base += stride) {
         const unsigned long long e = base + lane;
@@ -295,40 +326,55 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
         uint32_t u = 0, v = 0;
         if (valid) { u = b.src[e]; v = b.dst[e]; }
         const bool loop = valid && u == v;
-        // with colours (one hash group) the edge's colour decides whether it is kept and rides in its
-        // list entries: one hash serves both
-        uint32_t cj = 0u;
+        // with stored colours the edge's colours decide whether it is kept and ride with its list
+        // entries (in the entries' top bits for one hash group, in a word per entry for several): the
+        // same hashes serve both
+        uint32_t cj = 0u, cw = 0u;
         bool kept;
-        if (d.colours) {
+        if (d.colours == kColInEntry) {
             uint32_t i;
             const uint32_t j = colour_of(u, v, d.seed, d.fm);
             kept = valid && u != v && processor_of(d, 0u, j, i);
             cj = j << kIdBits;
+        } else if (has_words(d)) {
+            bool any = false;
+            uint64_t sk = group_seed(d.seed, d.kbeg);
+            for (uint32_t k = d.kbeg; k < d.kend; ++k, sk += kGoldenGamma) {
+                uint32_t i;
+                const uint32_t j = colour_of(u, v, sk, d.fm);
+                cw |= j << (k * d.cbits);
+                any |= processor_of(d, k, j, i);
+            }
+            kept = valid && u != v && any;
         } else {
             kept = valid && u != v && kept_by_any(d, u, v);
         }
         uint32_t key = kNoKey;
         WorkItem it{};
         if (valid && u != v) {
-            const uint2 mu = d.meta[u], mv = d.meta[v];
+            const uint4 mu = d.meta[u], mv = d.meta[v];
             if (kept && block_fits(d, 1, mu.x, table_lg(mu.y)) && block_fits(d, 1, mv.x, table_lg(mv.y))) {
                 const uint32_t t = (uint32_t)(b.t0 + e);
                 const uint32_t lu = table_lg(mu.y), lv = table_lg(mv.y);
                 bool ok = table_insert(d.pool, 4ull * mu.x, lu, v, t);
                 ok &= table_insert(d.pool, 4ull * mv.x, lv, u, t);
                 if (!ok) atomicOr(&ct->status, kStInternal);
-                // list positions: add[x] counts this batch's entries of x back down to zero
-                const uint32_t pu = mu.y - atomicSub(&d.add[u], 1u), pv = mv.y - atomicSub(&d.add[v], 1u);
+                // list positions: meta[x].z counts this batch's entries of x back down to zero
+                const uint32_t pu = mu.y - atomicSub(&d.meta[u].z, 1u), pv = mv.y - atomicSub(&d.meta[v].z, 1u);
                 if (REPT_CHECK(ct, 2, pu, list_slots(lu)) && REPT_CHECK(ct, 2, pv, list_slots(lv))) {
                     d.pool[4ull * mu.x + (1ull << lu) + pu] = make_uint2(v | cj, t);
                     d.pool[4ull * mv.x + (1ull << lv) + pv] = make_uint2(u | cj, t);
+                    if (has_words(d)) {
+                        list_words(d.pool, mu.x, lu)[pu] = cw;
+                        list_words(d.pool, mv.x, lv)[pv] = cw;
+                    }
                 }
                 if (d.edge_ends) d.edge_ends[t] = make_uint2(u, v);
             }
             // an edge can close wedges only if both endpoints have stored edges
             if (mu.y != 0u && mv.y != 0u) {
                 const bool u_small = mu.y <= mv.y;
-                const uint2 ms = u_small ? mu : mv, ml = u_small ? mv : mu;
+                const uint4 ms = u_small ? mu : mv, ml = u_small ? mv : mu;
                 it.s = u_small ? u : v;
                 it.l = u_small ? v : u;
                 it.off_s = ms.x;
@@ -346,54 +392,69 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
             if (key != kNoKey && lane == (unsigned)(__ffs(peers) - 1))
                 atomicAdd(&d.hist[key], (uint32_t)__popc(peers));
         }
-        warp_reserve(&ct->self_loops, loop ? 1ull : 0ull);
-        warp_reserve(&ct->stored, kept ? 1ull : 0ull);
+        n_loops += loop ? 1ull : 0ull;
+        n_kept += kept ? 1ull : 0ull;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_loops += __shfl_down_sync(0xFFFFFFFFu, n_loops, o);
+        n_kept += __shfl_down_sync(0xFFFFFFFFu, n_kept, o);
+    }
+    if (lane == 0) {
+        if (n_loops) atomicAdd(&ct->self_loops, n_loops);
+        if (n_kept) atomicAdd(&ct->stored, n_kept);
     }
 }
 
 // Exclusive scan of the counting-sort histogram (one block of 1024 threads): counts become the
-// first position of each key, and the class boundaries are recorded.
+// first position of each key, and the class boundaries are recorded.  The counters are scanned in
+// chunks of 4096, thread t holding counters 4t..4t+3 of a chunk (one coalesced 16-byte load).
 __device__ __forceinline__ void k_sort_scan_body(const StreamDev& d) {
-    constexpr uint32_t kPer = kSortBuckets / 1024;
-    __shared__ uint32_t warp_sum[32];
+    constexpr uint32_t kChunk = 4u * 1024u;
+    static_assert(kSortBuckets % kChunk == 0 && kKeyBuckets % kChunk == 0, "scan chunks");
+    __shared__ uint32_t warp_sum[33];
     if (d.ctrl->status) return;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
-    uint32_t local[kPer];
-    uint32_t sum = 0;
-#pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) {
-        local[k] = d.hist[tid * kPer + k];
-        sum += local[k];
-    }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= (uint32_t)o) incl += y;
-    }
-    if (lane == 31) warp_sum[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t w = warp_sum[lane], wi = w;
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < kSortBuckets; base += kChunk) {
+        const uint4 v = reinterpret_cast<const uint4*>(d.hist + base)[tid];
+        const uint32_t sum = v.x + v.y + v.z + v.w;
+        uint32_t incl = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-            if (lane >= (uint32_t)o) wi += y;
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
         }
-        warp_sum[lane] = wi - w;
-    }
-    __syncthreads();
-    uint32_t run = warp_sum[wid] + incl - sum;
+        if (lane == 31) warp_sum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const uint32_t w = warp_sum[lane];
+            uint32_t wi = w;
 #pragma unroll
-    for (uint32_t k = 0; k < kPer; ++k) {
-        const uint32_t key = tid * kPer + k;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+                if (lane >= (uint32_t)o) wi += y;
+            }
+            warp_sum[lane] = wi - w;
+            if (lane == 31) warp_sum[32] = wi;  // the chunk's total
+        }
+        __syncthreads();
+        uint32_t run = carry + warp_sum[wid] + incl - sum;
+        const uint32_t key = base + 4u * tid;
         if (key % kKeyBuckets == 0u) d.ctrl->bin_start[key / kKeyBuckets] = run;
-        d.hist[key] = run;
-        run += local[k];
+        uint4 o;
+        o.x = run;
+        run += v.x;
+        o.y = run;
+        run += v.y;
+        o.z = run;
+        run += v.z;
+        o.w = run;
+        reinterpret_cast<uint4*>(d.hist + base)[tid] = o;
+        carry += warp_sum[32];
+        __syncthreads();  // warp_sum is reused by the next chunk
     }
-    __syncthreads();
-    if (tid == 1023) {  // totals: the last thread's running sum is the number of items
-        unsigned long long prev = run;
+    if (tid == 0) {  // totals (thread 0 wrote every class start): carry is the number of items
+        unsigned long long prev = carry;
         for (int c = kBins - 1; c >= 0; --c) {
             d.ctrl->bin_count[c] = prev - d.ctrl->bin_start[c];
             prev = d.ctrl->bin_start[c];
@@ -458,7 +519,7 @@ __global__ void k_check_dups(StreamDev d, BatchDev b, unsigned long long mask) {
     for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < b.n; e += stride) {
         const uint32_t u = b.src[e], v = b.dst[e];
         if (u == v || u >= d.n_nodes || v >= d.n_nodes) continue;
-        const uint2 mu = d.meta[u];
+        const uint4 mu = d.meta[u];
         uint32_t ns;
         if (mu.y != 0u && table_find(d.pool, 4ull * mu.x, table_lg(mu.y), v, ns) != kEmptyId) dup = true;
         const unsigned long long key = ((unsigned long long)(u < v ? u : v) << 32) | (u < v ? v : u);
@@ -492,7 +553,7 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
     if (!REPT_CHECK(d.ctrl, 9, max(w, max(s, l)), d.n_nodes)) return 0u;
     uint32_t found = 0, found2 = 0;
     uint32_t t_sw = kEmptyId, t_lw = kEmptyId;
-    for (uint32_t k = 0; k < d.groups; ++k) {
+    for (uint32_t k = d.kbeg; k < d.kend; ++k) {
         const uint64_t sk = group_seed(d.seed, k);
         const uint32_t js = colour_of(s, w, sk, d.fm);
         uint32_t i;
@@ -508,7 +569,7 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
             if (d.pair_tau) {
                 if (t_sw == kEmptyId) {  // the wedge's two stream indices, looked up once
                     uint32_t ns;
-                    const uint2 ms = d.meta[s], ml = d.meta[l];
+                    const uint4 ms = d.meta[s], ml = d.meta[l];
                     t_sw = table_find(d.pool, 4ull * ms.x, table_lg(ms.y), w, ns);
                     t_lw = table_find(d.pool, 4ull * ml.x, table_lg(ml.y), w, ns);
                 }
@@ -585,7 +646,11 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
         const uint2 es = fits ? d.pool[at] : make_uint2(kEmptyId, kEmptyId);
         if (WORK && j == 0) { wk.entries += x.cnt_s; wk.slots += x.cnt_s; }
         const uint32_t ws = es.x & id_mask(d);
-        if (es.y < x.t && (!d.colours || wedge_may_count(d, x.l, ws, es.x >> kIdBits))) {
+        bool pass = es.y < x.t;
+        if (d.colours == kColInEntry) pass = pass & wedge_may_count(d, x.l, ws, es.x >> kIdBits);
+        else if (pass && has_words(d) && block_fits(d, 12, x.off_s, x.lgs & 0xFFu))
+            pass = words_may_count(d, x.l, ws, list_words(d.pool, x.off_s, x.lgs & 0xFFu)[j]);
+        if (pass) {
             uint32_t nslots = 0;
             const uint32_t tl = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, ws, nslots);
             if (WORK) { ++wk.probes; wk.pslots += nslots; }
@@ -610,17 +675,23 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
 constexpr uint32_t kGrabMid = REPT_GRAB_MID;  // class 4 items (33..256 entries) claimed per atomic
 constexpr uint32_t kGrabHub = REPT_GRAB_HUB;  // class 5 items (more entries) claimed per atomic
 constexpr int kQueue = 192;  // one partial round (< 64 keys) + 128 new keys
+
 #ifndef REPT_PROBES_PER_LANE
 #define REPT_PROBES_PER_LANE 2
 #endif
 constexpr int kProbesPerLane = REPT_PROBES_PER_LANE;  // probes each lane keeps in flight (warp path)
+#ifndef REPT_WORDS_BLOCKS
+#define REPT_WORDS_BLOCKS 6
+#endif
 
-// COLOURED: the variant for streams that keep colours (hash-bound; the next pass is prefetched); the
-// other variant serves streams without them (probe-bound; fewer registers, more warps per SM).
+// MODE: the colour storage this instantiation tests (kColInEntry: hash-bound, the next pass is
+// prefetched; kColWords: one hash per hash group and entry; kColNone: probe-bound, fewer registers,
+// more warps per SM).  A stream whose colours differ from MODE is served as kColNone.
 // `push(has, w)` (warp-collective) takes each probed key w and whether it closed a wedge.
-template <bool WORK, bool COLOURED, class Push>
+template <bool WORK, int MODE, class Push>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, uint32_t* queue, Work& wk,
                                                Push&& push) {
+    constexpr bool PREFETCH = MODE == (int)kColInEntry;
     constexpr uint32_t kRound = 32u * kProbesPerLane;
     static_assert(kRound - 1 + 128 <= kQueue, "key queue too small");
     const unsigned lane = threadIdx.x & 31u;
@@ -634,29 +705,39 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
     // load; with colours, each entry's id and colour share its first word
     const unsigned long long at_s = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu));
     const uint4* list = reinterpret_cast<const uint4*>(d.pool + at_s);
-    const bool cols = COLOURED && d.colours;
+    const bool cols = MODE == (int)kColInEntry && d.colours == kColInEntry;
+    const bool wcols = MODE == (int)kColWords && d.colours == kColWords;
+    // kColWords: the colour words of the entries, two per 8-byte load
+    const uint2* words = reinterpret_cast<const uint2*>(list_words(d.pool, x.off_s, x.lgs & 0xFFu));
     const uint32_t mask = id_mask(d);
     const uint32_t* keys_l = reinterpret_cast<const uint32_t*>(d.pool + base_l);
     const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
     const uint32_t cap_l = 1u << lg_l;
     const unsigned below = (1u << lane) - 1u;
-    // COLOURED: the next pass's entries are loaded while the current pass is tested
+    // PREFETCH: the next pass's entries are loaded while the current pass is tested
     uint4 nq[2];
+    uint2 nw[2];
     auto load_pass = [&](uint32_t j0) {
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
             const uint32_t jj = j0 + 64u * half + 2u * lane;
             nq[half] = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-            if (jj < n_s) nq[half] = list[jj >> 1];
+            nw[half] = make_uint2(0u, 0u);
+            if (jj < n_s) {
+                nq[half] = list[jj >> 1];
+                if (wcols) nw[half] = words[jj >> 1];
+            }
         }
     };
-    if (COLOURED) load_pass(0u);
+    if (PREFETCH) load_pass(0u);
     uint32_t n_q = 0;
+
     for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
         if (!REPT_CHECK(d.ctrl, 8, n_q, kRound)) break;
-        if (!COLOURED) load_pass(j0);
+        if (!PREFETCH) load_pass(j0);
         const uint4 cq[2] = {nq[0], nq[1]};
-        if (COLOURED && j0 + 128u < n_s) load_pass(j0 + 128u);
+        const uint2 cw[2] = {nw[0], nw[1]};
+        if (PREFETCH && j0 + 128u < n_s) load_pass(j0 + 128u);
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
             const uint32_t jj = j0 + 64u * half + 2u * lane;
@@ -664,8 +745,11 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
             const uint32_t w1 = q.x & mask, w2 = q.z & mask;
             bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
             if (cols) {
-                a1 = a1 && wedge_may_count(d, x.l, w1, q.x >> kIdBits);
-                a2 = a2 && wedge_may_count(d, x.l, w2, q.z >> kIdBits);
+                a1 = a1 & wedge_may_count(d, x.l, w1, q.x >> kIdBits);
+                a2 = a2 & wedge_may_count(d, x.l, w2, q.z >> kIdBits);
+            } else if (wcols) {
+                a1 = a1 && words_may_count(d, x.l, w1, cw[half].x);
+                a2 = a2 && words_may_count(d, x.l, w2, cw[half].y);
             }
             const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
             if (a1) queue[n_q + __popc(m1 & below)] = w1;
@@ -744,7 +828,7 @@ __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, int cls, unsi
 
 // Warp classes: a warp claims `grab` consecutive items per atomic on the class cursor (one cursor is
 // shared by every warp of the grid, so claiming one item at a time serialises on it).
-template <bool WORK, bool COLOURED>
+template <bool WORK, int MODE>
 __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint32_t grab, unsigned long long* s_proc,
                                                uint32_t* queue, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
@@ -758,7 +842,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint
         const unsigned long long i1 = i0 + grab < count ? i0 + grab : count;
         for (unsigned long long i = i0; i < i1; ++i) {
             const WorkItem x = items[i];
-            intersect_warp<WORK, COLOURED>(d, x, queue, wk, [&](bool has, uint32_t w) {
+            intersect_warp<WORK, MODE>(d, x, queue, wk, [&](bool has, uint32_t w) {
                 mq_push<WORK>(d, mq, has, x.s, x.l, w, s_proc, wk);
             });
         }
@@ -768,7 +852,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint
 // UpdateTriangleCNT for every edge of the batch.  The edges were sorted into work classes by
 // k_insert; warps claim work dynamically, largest class first.  Dynamic shared memory: c uint64
 // counters (tau^(i) of this block).  WORK = true also tallies the table reads.
-template <bool WORK, bool COLOURED>
+template <bool WORK, int MODE>
 __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const BatchDev& b) {
     extern __shared__ unsigned long long s_proc[];
     __shared__ uint32_t s_queue[256 / 32][kQueue];
@@ -798,9 +882,9 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
                 p0 = p1;
             }
         };
-        drain_warp_bin<WORK, COLOURED>(d, 5, kGrabHub, s_proc, queue, mq, wk);
+        drain_warp_bin<WORK, MODE>(d, 5, kGrabHub, s_proc, queue, mq, wk);
         mark(5);
-        drain_warp_bin<WORK, COLOURED>(d, 4, kGrabMid, s_proc, queue, mq, wk);
+        drain_warp_bin<WORK, MODE>(d, 4, kGrabMid, s_proc, queue, mq, wk);
         mark(4);
         drain_tile_bin<32, WORK>(d, 3, s_proc, mq, wk);
         mark(3);
@@ -903,7 +987,7 @@ __device__ __forceinline__ void gq_flush(const StreamDev* __restrict__ ds, Group
         const StreamDev& d = ds[q.sid[i]];
         const uint32_t s = q.s[i], l = q.l[i], w = q.w[i];
         uint32_t found = 0;
-        for (uint32_t k = 0; k < d.groups; ++k) {
+        for (uint32_t k = d.kbeg; k < d.kend; ++k) {
             const uint64_t sk = group_seed(d.seed, k);
             const uint32_t js = colour_of(s, w, sk, d.fm);
             uint32_t i;
@@ -991,7 +1075,7 @@ __device__ __forceinline__ void group_drain_tiles(const StreamDev* __restrict__ 
                                       block_fits(d, 4, x.off_l, x.lgs >> 8);
                     const uint2 es = fits ? d.pool[at] : make_uint2(kEmptyId, kEmptyId);
                     const uint32_t ws = es.x & id_mask(d);
-                    if (es.y < x.t && (!d.colours || wedge_may_count(d, x.l, ws, es.x >> kIdBits))) {
+                    if (es.y < x.t && (d.colours != kColInEntry || wedge_may_count(d, x.l, ws, es.x >> kIdBits))) {
                         uint32_t nslots = 0;
                         has = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, ws, nslots) < x.t;
                         w = ws;
@@ -1022,7 +1106,7 @@ __device__ __forceinline__ void group_drain_warps(const StreamDev* __restrict__ 
             sid = group_stream_of(pc, k, i, sid);
             const StreamDev& d = ds[sid];
             const WorkItem x = group_item(d, cls, i - pc[sid]);
-            intersect_warp<false, true>(d, x, queue, wk, [&](bool has, uint32_t w) {
+            intersect_warp<false, (int)kColInEntry>(d, x, queue, wk, [&](bool has, uint32_t w) {
                 gq_push(ds, q, has, sid, x.s, x.l, w);
             });
         }
@@ -1207,15 +1291,27 @@ __global__ void k_sort_scatter_multi(const StreamDev* __restrict__ ds, const Bat
     k_sort_scatter_body(sd, sb);
 }
 
-// Streams that keep colours (one hash group, m <= 256): 5 blocks of 256 threads per SM.
+// Streams whose entries carry their colour (one hash group, m <= 256): 5 blocks of 256 threads per SM.
+#ifndef REPT_COLOURED_BLOCKS
+#define REPT_COLOURED_BLOCKS 5
+#endif
 template <bool WORK>
-__global__ void __launch_bounds__(256, 5) k_intersect(StreamDev d, BatchDev b) { k_intersect_body<WORK, true>(d, b); }
+__global__ void __launch_bounds__(256, REPT_COLOURED_BLOCKS) k_intersect(StreamDev d, BatchDev b) {
+    k_intersect_body<WORK, (int)kColInEntry>(d, b);
+}
 
-// Streams without colours (several hash groups or m > 256): every probe is issued, so the kernel
-// waits on memory and wants every warp an SM can hold.
+// Streams whose entries have colour words (several hash groups): hashes per entry, and probes for
+// about groups/m of the entries.
+template <bool WORK>
+__global__ void __launch_bounds__(256, REPT_WORDS_BLOCKS) k_intersect_words(StreamDev d, BatchDev b) {
+    k_intersect_body<WORK, (int)kColWords>(d, b);
+}
+
+// Streams without stored colours (parallel MASCOT with several samplers, or too many groups for a
+// word): every probe is issued, so the kernel waits on memory and wants every warp an SM can hold.
 template <bool WORK>
 __global__ void __launch_bounds__(256, 8) k_intersect_probe(StreamDev d, BatchDev b) {
-    k_intersect_body<WORK, false>(d, b);
+    k_intersect_body<WORK, (int)kColNone>(d, b);
 }
 
 template <bool WORK>
@@ -1228,7 +1324,7 @@ __global__ void __launch_bounds__(256, 5) k_intersect_multi(const StreamDev* __r
         sb = bs[blockIdx.y];
     }
     __syncthreads();
-    k_intersect_body<WORK, true>(sd, sb);
+    k_intersect_body<WORK, (int)kColInEntry>(sd, sb);
 }
 
 // tau_hat_v = f * sum_i tau_v^(i), f formed in double on the host.

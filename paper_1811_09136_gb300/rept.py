@@ -37,7 +37,8 @@ class ReptError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("m", ctypes.c_uint32), ("c", ctypes.c_uint32), ("seed", ctypes.c_uint64),
                 ("n_nodes", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("expected_edges", ctypes.c_uint64),
-                ("max_batch", ctypes.c_uint64), ("tile_max", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("max_batch", ctypes.c_uint64), ("tile_max", ctypes.c_uint32), ("proc_begin", ctypes.c_uint32),
+                ("proc_end", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("reserved2", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -94,6 +95,9 @@ def load():
             "rept_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "rept_kernel_launches": (ctypes.c_uint64, []),
             "rept_ingest_multi": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_uint32, _vp]),
+            "rept_estimates_from_counts": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp,
+                                                          ctypes.c_uint32, ctypes.POINTER(ctypes.c_double), _vp,
+                                                          _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -144,13 +148,17 @@ class ReptStream:
     """One edge stream counted by REPT on the current CUDA device (see include/rept.h)."""
 
     def __init__(self, n_nodes: int, m: int, c: int, seed: int = 1, expected_edges: int = 0,
-                 max_batch: int = 1 << 20, flags: int = 0, stream=None, tile_max: int = 0):
+                 max_batch: int = 1 << 20, flags: int = 0, stream=None, tile_max: int = 0,
+                 proc_range: tuple[int, int] | None = None):
+        """``proc_range=(b, e)`` keeps processors b..e-1 only (a colour shard, see rept_config)."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ReptStream needs a CUDA device; there is no CPU fallback")
         lib = load()
         self.n_nodes, self.m, self.c, self.seed = int(n_nodes), int(m), int(c), int(seed)
-        cfg = Config(self.m, self.c, self.seed, self.n_nodes, flags, expected_edges, max_batch, tile_max, 0)
+        self.flags = int(flags)
+        b, e = proc_range if proc_range is not None else (0, 0)
+        cfg = Config(self.m, self.c, self.seed, self.n_nodes, flags, expected_edges, max_batch, tile_max, b, e, 0, 0)
         h = ctypes.c_void_p()
         _check(lib.rept_create(ctypes.byref(cfg), _cur_stream(stream), ctypes.byref(h)), "rept_create")
         self._h = h
@@ -296,6 +304,28 @@ class ReptStream:
         _check(self._lib.rept_kernel_times(self._h, ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(n, ctypes.c_void_p),
                                            int(clear)), "rept_kernel_times")
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNELS)}
+
+
+def estimates_from_counts(m: int, c: int, proc: np.ndarray, local=None, flags: int = 0, stream=None):
+    """rept_estimates_from_counts: (tau_hat, tau_hat_v as a float64 CUDA tensor or None) from integer
+    counts, e.g. summed over colour shards.  ``proc``: numpy uint64 [c]; ``local``: int64 CUDA tensor
+    of sum_i tau_v^(i) or None."""
+    import torch
+    lib = load()
+    proc = np.ascontiguousarray(proc, dtype=np.uint64)
+    if proc.size != c:
+        raise ValueError("proc must hold c counters")
+    g = ctypes.c_double()
+    out = None
+    if local is not None:
+        out = torch.empty(local.numel(), dtype=torch.float64, device=local.device)
+    _check(lib.rept_estimates_from_counts(m, c, flags, ctypes.c_void_p(proc.ctypes.data),
+                                          ctypes.c_void_p(local.data_ptr()) if local is not None else None,
+                                          local.numel() if local is not None else 0, ctypes.byref(g),
+                                          ctypes.c_void_p(out.data_ptr()) if out is not None else None,
+                                          _cur_stream(stream) if local is not None else None),
+           "rept_estimates_from_counts")
+    return g.value, out
 
 
 def ingest_multi(handles, srcs, dsts, stream=None):
