@@ -46,9 +46,10 @@ def test_complete_graph_closed_form():
         assert g == float(math.comb(n, 3))
 
 
-@pytest.mark.parametrize("m,c", [(10, 10), (10, 3), (4, 8), (1, 1)])
+@pytest.mark.parametrize("m,c", [(10, 10), (10, 3), (4, 8), (1, 1), (300, 300), (300, 120)])
 def test_powerlaw_20k(m, c):
-    """Chung-Lu, 20,000 nodes, exponent 2.3, 200,000 edges: whole stream, 2^10 and 2^16 batches."""
+    """Chung-Lu, 20,000 nodes, exponent 2.3, 200,000 edges: whole stream, 2^10 and 2^16 batches.
+    m = 300 keeps a colour word per list entry (too many colours for the entry's top 8 bits)."""
     s = gg.cached("powerlaw_20k")
     ref = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, 1, pair_counters=False)
     ref_g, ref_loc = O.estimates(m, c, ref, s.n_nodes)
@@ -153,7 +154,8 @@ def test_fixed_pool_capacity_error():
 @pytest.mark.parametrize("n", [1 << 24, 1 << 27])
 def test_large_node_ids(n):
     """Ids near the top of a 2^24-node space (the largest whose list entries carry colours in their
-    top 8 bits) and of a 2^27-node space (no colours kept; meta/local arrays of 1-2 GB)."""
+    top 8 bits) and of a 2^27-node space (colours in a word per list entry; node records and local
+    counts of 2 GB and 1 GB)."""
     base = gg.gnp(60, 0.25, 16, 17)
     off = np.uint32(n - 64)
     s = gg.EdgeStream(base.src + off, base.dst + off, n)
