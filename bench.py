@@ -429,7 +429,9 @@ def batched_leg(args, world, rank, pg, digests, e2e=False, chunks=(1 << 16, 1 <<
     b, tm, timings = batched.autotune([streams[i] for i in sample], [params[i] for i in sample],
                                       key=f"mix{args.streams}")
     res_b, t_b = batched.run_batched(streams, params, batch=b, tile_max=tm)
+    res_q, t_q = batched.run_batched(streams, params, batch=b, tile_max=tm, persistent=True)
     res_p, t_p = batched.run_plain(streams, params, batch=b, tile_max=tm)
+    assert all(np.array_equal(x.proc, y.proc) and np.array_equal(x.local, y.local) for x, y in zip(res_b, res_q))
     same = all(np.array_equal(x.proc, y.proc) and np.array_equal(x.local, y.local) for x, y in zip(res_b, res_p))
     assert same, "batched and plain counts differ"
     checks = [compare_with_oracle(digests, digest_key(f"mix{MIX_SEED}#{sp.index}", sp.m, sp.m, sp.hash_seed),
@@ -439,20 +441,26 @@ def batched_leg(args, world, rank, pg, digests, e2e=False, chunks=(1 << 16, 1 <<
     exact = {"streams": len(checks), "checked": len(checked),
              "identical": bool(checked) and all(c["identical"] for c in checked)}
     t_b = max_over_ranks(pg, t_b)
+    t_q = max_over_ranks(pg, t_q)
     t_p = max_over_ranks(pg, t_p)
     out = {"streams": args.streams, "edges": E, "value": world * E / t_b, "unit": "edges/s", "seconds": t_b,
            "batch": b, "tile_max": tm, "autotune_s": timings, "generation_s": gen_s,
+           "persistent": {"value": world * E / t_q, "unit": "edges/s", "seconds": t_q,
+                          "what": "one cooperative launch per round runs every step for every stream"},
            "plain_loop": {"value": world * E / t_p, "unit": "edges/s", "seconds": t_p},
            "batched_over_plain": t_p / t_b, "identical_counts": same, "exact": exact, "by_chunk": {}}
     for ch in chunks:
         rb, tb = batched.run_batched(streams, params, batch=ch, tile_max=tm)
+        rq, tq = batched.run_batched(streams, params, batch=ch, tile_max=tm, persistent=True)
         rp, tp = batched.run_plain(streams, params, batch=ch, tile_max=tm)
         ok = all(np.array_equal(x.proc, y.proc) and np.array_equal(x.local, y.local) and
-                 np.array_equal(x.proc, z.proc) for x, y, z in zip(rb, rp, res_b))
+                 np.array_equal(x.proc, z.proc) and np.array_equal(x.local, q.local)
+                 for x, y, z, q in zip(rb, rp, res_b, rq))
         assert ok, f"counts differ at chunk {ch}"
-        tb, tp = max_over_ranks(pg, tb), max_over_ranks(pg, tp)
-        out["by_chunk"][str(ch)] = {"batched": world * E / tb, "plain_loop": world * E / tp,
-                                    "batched_over_plain": tp / tb, "identical_counts": ok}
+        tb, tq, tp = max_over_ranks(pg, tb), max_over_ranks(pg, tq), max_over_ranks(pg, tp)
+        out["by_chunk"][str(ch)] = {"batched": world * E / tb, "persistent": world * E / tq,
+                                    "plain_loop": world * E / tp, "batched_over_plain": tp / tb,
+                                    "persistent_over_plain": tp / tq, "identical_counts": ok}
     if e2e:
         rb, te = batched.run_batched(streams, params, batch=b, tile_max=tm, host_io=True)
         assert all(np.array_equal(x.proc, y.proc) for x, y in zip(rb, res_b))

@@ -54,8 +54,8 @@ extern "C" {
 #define REPT_E_CAPACITY (-3)  /* REPT_FLAG_FIXED_POOL set and the adjacency pool is full (batch not applied) */
 #define REPT_E_NOMEM (-4)     /* a device or pinned-host allocation failed */
 #define REPT_E_CUDA (-5)      /* a CUDA runtime call failed */
-#define REPT_E_TIMEOUT (-6)   /* reserved for a bounded device-side wait that gives up; no kernel of this
-                                 library waits on a flag or on another kernel, so none returns it */
+#define REPT_E_TIMEOUT (-6)   /* a bounded grid-wide wait of the persistent group kernel
+                                 (REPT_GROUP_PERSISTENT) ran out; the call's batches were not applied */
 #define REPT_E_INTERNAL (-7)  /* a device-side invariant failed (bounded probe found no slot) */
 #define REPT_E_SCRATCH (-8)   /* rept_count_noalloc: the problem does not fit its fixed scratch area */
 #define REPT_E_DUPLICATE (-9) /* REPT_FLAG_CHECK_DUPS: a repeated edge (device-detected, batch not applied) */
@@ -288,9 +288,21 @@ void rept_destroy(rept_state* s);
  *
  * rept_group_create: max_streams >= 1; flags REPT_GROUP_GRAPH captures the
  * launch sequence in a CUDA graph and replays it on later calls with the same
- * shape (used only when no stream's pool can run out during the call).
+ * shape (used only when no stream's pool can run out during the call);
+ * REPT_GROUP_PERSISTENT makes that sequence one cooperative launch (see the
+ * flag).  REPT_E_CUDA when the device cannot launch cooperative kernels.
  */
 #define REPT_GROUP_GRAPH 1u
+#define REPT_GROUP_PERSISTENT 2u  /* one cooperative launch per call runs every step of the batch path
+                                     for every stream, the streams' work dealt out over one co-resident
+                                     grid, with grid-wide waits between the steps; each wait is bounded
+                                     in time, and when it runs out the call's streams report
+                                     REPT_E_TIMEOUT (nothing is applied).  Used when no stream's pool can
+                                     run out during the call (otherwise the launch-per-step path runs);
+                                     with REPT_GROUP_GRAPH the launch is replayed from a CUDA graph */
+#define REPT_GROUP_TEST_TIMEOUT 4u /* test hook for the timeout path, with REPT_GROUP_PERSISTENT only: the
+                                      first grid-wide wait expects one block more than the grid holds,
+                                      so it runs out after 0.1 s; REPT_E_INVAL without the other flag */
 typedef struct rept_group rept_group;
 int rept_group_create(uint32_t max_streams, uint32_t flags, rept_group** out);
 

@@ -25,13 +25,17 @@ import numpy as np
 
 from . import graphgen, rept
 
-_GROUP_GRAPH = 1
+GROUP_GRAPH = 1
+GROUP_PERSISTENT = 2
+GROUP_TEST_TIMEOUT = 4
 
 
 class ReptGroup:
-    """Binding of rept_group_create / rept_group_ingest / rept_group_destroy."""
+    """Binding of rept_group_create / rept_group_ingest / rept_group_destroy.  With `persistent`
+    every call is one cooperative launch running all steps for all streams (REPT_GROUP_PERSISTENT);
+    `test_timeout` is the test hook that makes its first grid-wide wait run out."""
 
-    def __init__(self, max_streams: int, graph: bool = True):
+    def __init__(self, max_streams: int, graph: bool = True, persistent: bool = False, test_timeout: bool = False):
         lib = rept.load()
         lib.rept_group_create.restype = ctypes.c_int
         lib.rept_group_create.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]
@@ -43,8 +47,9 @@ class ReptGroup:
         self._lib = lib
         self.max_streams = int(max_streams)
         h = ctypes.c_void_p()
-        rept._check(lib.rept_group_create(max_streams, _GROUP_GRAPH if graph else 0, ctypes.byref(h)),
-                    "rept_group_create")
+        flags = (GROUP_GRAPH if graph else 0) | (GROUP_PERSISTENT if persistent else 0) | \
+            (GROUP_TEST_TIMEOUT if test_timeout else 0)
+        rept._check(lib.rept_group_create(max_streams, flags, ctypes.byref(h)), "rept_group_create")
         self._h = h
         self._hs = (ctypes.c_void_p * max_streams)()
         self._src = (ctypes.c_void_p * max_streams)()
@@ -200,14 +205,14 @@ def _result_buffers(c: int):
 
 def run_batched(streams, params, batch: int = 1 << 18, tile_max: int = 32, graph: bool = True,
                 budget: int | None = None, local_estimates: bool = False, presize: bool = True,
-                host_io: bool = False):
+                host_io: bool = False, persistent: bool = False):
     """All streams through one rept_group, batch edges per stream per round.  `params[i]` is
     (m, c, seed).  With `presize` every pool is sized for its whole stream up front (no round needs
     a pool check); without it pools start small and grow (one host check per round).  With
     `host_io` the timed region also holds the copy of every stream's edges from pinned host memory
     to the device and the copy of each stream's tau_hat, tau^(i) and status word back to pinned
-    host memory (end to end).  Returns (results, seconds of device work incl. per-round host launch
-    cost)."""
+    host memory (end to end).  With `persistent` each round is one cooperative launch of every step
+    for every stream.  Returns (results, seconds of device work incl. per-round host launch cost)."""
     import torch
     budget = budget or _device_budget()
     results = [None] * len(streams)
@@ -226,7 +231,7 @@ def run_batched(streams, params, batch: int = 1 << 18, tile_max: int = 32, graph
             else:
                 srcs.append(torch.from_numpy(s.src.view(np.int32)).cuda())
                 dsts.append(torch.from_numpy(s.dst.view(np.int32)).cuda())
-        group = ReptGroup(len(wave), graph=graph)
+        group = ReptGroup(len(wave), graph=graph, persistent=persistent)
         rounds = max((len(streams[i]) + batch - 1) // batch for i in wave)
         torch.cuda.synchronize()
         t = time.perf_counter()

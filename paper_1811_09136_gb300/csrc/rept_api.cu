@@ -860,6 +860,12 @@ struct rept_group {
     unsigned long long shape[2][6] = {{0}};  // what each slot's graph was captured for
     int slot = 0;
     cudaStream_t capture = nullptr;  // private stream the graphs are captured on (the legacy stream cannot be)
+    // REPT_GROUP_PERSISTENT: the grid barrier state, its per-launch initial value (pinned), and the
+    // co-resident grid of k_group_persistent
+    GroupSync* d_sync = nullptr;
+    GroupSync* h_sync = nullptr;
+    int persist_grid = 0;
+    bool persist_graph_ok = true;  // a captured cooperative launch instantiated (else launched directly)
 };
 
 namespace {
@@ -899,12 +905,37 @@ int enqueue_group(rept_group* g, const GroupShape& sh, cudaStream_t st, int part
     return REPT_OK;
 }
 
+// Time a grid-wide wait of the persistent kernel may take before it gives up: far above any step
+// (a step of a 2^20-edge batch takes milliseconds), or 0.1 s under REPT_GROUP_TEST_TIMEOUT.
+constexpr unsigned long long kPersistWaitNs = 20ull * 1000 * 1000 * 1000;
+constexpr unsigned long long kTestWaitNs = 100ull * 1000 * 1000;
+
+// Enqueue one round as a single cooperative launch: the barrier state is reset from pinned memory
+// first (a previous launch that gave up may have left it mid-barrier).
+int enqueue_persistent(rept_group* g, const GroupShape& sh, cudaStream_t st) {
+    REPT_CUDA(cudaMemcpyAsync(g->d_sync, g->h_sync, sizeof(GroupSync), cudaMemcpyHostToDevice, st));
+    const StreamDev* ds = g->d_sd;
+    const BatchDev* bs = g->d_bd;
+    uint32_t k = sh.k;
+    PersistShape ps{(uint32_t)sh.x_edge, (uint32_t)sh.x_big, (uint32_t)sh.x_huge};
+    unsigned long long* pref = g->d_pref;
+    unsigned long long* cursor = g->d_cursor;
+    GroupSync* gs = g->d_sync;
+    unsigned long long wait_ns = (g->flags & REPT_GROUP_TEST_TIMEOUT) ? kTestWaitNs : kPersistWaitNs;
+    void* args[] = {&ds, &bs, &k, &ps, &pref, &cursor, &gs, &wait_ns};
+    REPT_CUDA(cudaLaunchCooperativeKernel((const void*)k_group_persistent, dim3(g->persist_grid), dim3(256), args,
+                                          kPersistSmemWords * sizeof(uint32_t), st));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return REPT_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int rept_group_create(uint32_t max_streams, uint32_t flags, rept_group** out) {
     if (!out || max_streams == 0 || max_streams > 65535u) return REPT_E_INVAL;
+    if ((flags & REPT_GROUP_TEST_TIMEOUT) && !(flags & REPT_GROUP_PERSISTENT)) return REPT_E_INVAL;
     *out = nullptr;
     rept_group* g = new (std::nothrow) rept_group();
     if (!g) return REPT_E_NOMEM;
@@ -940,6 +971,19 @@ int rept_group_create(uint32_t max_streams, uint32_t flags, rept_group** out) {
         return fail(REPT_E_NOMEM);
     if ((flags & REPT_GROUP_GRAPH) && cudaStreamCreateWithFlags(&g->capture, cudaStreamNonBlocking) != cudaSuccess)
         return fail(REPT_E_CUDA);
+    if (flags & REPT_GROUP_PERSISTENT) {
+        int coop = 0, per_sm_p = 0;
+        if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
+            return fail(REPT_E_CUDA);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_p, k_group_persistent, 256,
+                                                          kPersistSmemWords * sizeof(uint32_t)) != cudaSuccess ||
+            per_sm_p < 1)
+            return fail(REPT_E_CUDA);
+        g->persist_grid = g->sm_count * per_sm_p;
+        if (cudaMalloc(&g->d_sync, sizeof(GroupSync)) != cudaSuccess) return fail(REPT_E_NOMEM);
+        if (cudaMallocHost(&g->h_sync, sizeof(GroupSync)) != cudaSuccess) return fail(REPT_E_NOMEM);
+        *g->h_sync = GroupSync{0u, 0u, 0u, (flags & REPT_GROUP_TEST_TIMEOUT) ? 1u : 0u};
+    }
     *out = g;
     return REPT_OK;
 }
@@ -954,6 +998,8 @@ void rept_group_destroy(rept_group* g) {
         if (g->h_bd[i]) cudaFreeHost(g->h_bd[i]);
     }
     if (g->h_req) cudaFreeHost(g->h_req);
+    if (g->h_sync) cudaFreeHost(g->h_sync);
+    cudaFree(g->d_sync);
     if (g->capture) cudaStreamDestroy(g->capture);
     cudaFree(g->d_sd);
     cudaFree(g->d_bd);
@@ -1031,7 +1077,11 @@ int rept_group_ingest(rept_group* g, rept_state* const* hs, const uint32_t* cons
         }
         if (grew) REPT_CUDA(cudaMemcpyAsync(g->d_sd, hsd, k * sizeof(StreamDev), cudaMemcpyHostToDevice, st));
         if ((rc = enqueue_group(g, sh, st, 2))) return rc;
+    } else if ((g->flags & REPT_GROUP_PERSISTENT) && !((g->flags & REPT_GROUP_GRAPH) && g->persist_graph_ok)) {
+        if ((rc = upload())) return rc;
+        if ((rc = enqueue_persistent(g, sh, st))) return rc;
     } else if (g->flags & REPT_GROUP_GRAPH) {
+        const bool persistent = (g->flags & REPT_GROUP_PERSISTENT) != 0;
         const unsigned long long key[6] = {k, (unsigned long long)sh.x_edge, (unsigned long long)sh.x_big,
                                            (unsigned long long)sh.x_huge, (unsigned long long)sh.x_int, sh.smem};
         bool same = g->exec[slot] != nullptr;
@@ -1049,18 +1099,30 @@ int rept_group_ingest(rept_group* g, rept_state* const* hs, const uint32_t* cons
             if (cudaMemcpyAsync(g->d_sd, hsd, k * sizeof(StreamDev), cudaMemcpyHostToDevice, cs) != cudaSuccess ||
                 cudaMemcpyAsync(g->d_bd, hbd, k * sizeof(BatchDev), cudaMemcpyHostToDevice, cs) != cudaSuccess)
                 rc_cap = REPT_E_CUDA;
-            if (!rc_cap) rc_cap = enqueue_group(g, sh, cs, 0);
+            const unsigned long long before = g_launches.load(std::memory_order_relaxed);
+            if (!rc_cap) rc_cap = persistent ? enqueue_persistent(g, sh, cs) : enqueue_group(g, sh, cs, 0);
             const cudaError_t e_end = cudaStreamEndCapture(cs, &graph);
+            cudaError_t e_inst = cudaErrorUnknown;
+            if (!rc_cap && e_end == cudaSuccess) e_inst = cudaGraphInstantiate(&g->exec[slot], graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            g_launches.store(before, std::memory_order_relaxed);  // captured, not launched
+            if (persistent && (rc_cap || e_end != cudaSuccess || e_inst != cudaSuccess)) {
+                // a cooperative launch that cannot be captured: launch it directly from now on
+                (void)cudaGetLastError();
+                g->exec[slot] = nullptr;
+                g->persist_graph_ok = false;
+                if ((rc = upload())) return rc;
+                if ((rc = enqueue_persistent(g, sh, st))) return rc;
+                REPT_CUDA(cudaEventRecord(g->slot_done[slot], st));
+                for (uint32_t i = 0; i < k; ++i) hs[i]->next_t += n[i];
+                return REPT_OK;
+            }
             if (rc_cap) return rc_cap;
-            if (e_end != cudaSuccess) return REPT_E_CUDA;
-            const cudaError_t e_inst = cudaGraphInstantiate(&g->exec[slot], graph, 0);
-            cudaGraphDestroy(graph);
-            if (e_inst != cudaSuccess) return REPT_E_CUDA;
+            if (e_end != cudaSuccess || e_inst != cudaSuccess) return REPT_E_CUDA;
             for (int j = 0; j < 6; ++j) g->shape[slot][j] = key[j];
-            g_launches.fetch_sub(10, std::memory_order_relaxed);  // captured, not launched
         }
         REPT_CUDA(cudaGraphLaunch(g->exec[slot], st));
-        g_launches.fetch_add(10, std::memory_order_relaxed);
+        g_launches.fetch_add(persistent ? 1 : 10, std::memory_order_relaxed);
     } else {
         if ((rc = upload())) return rc;
         if ((rc = enqueue_group(g, sh, st, 0))) return rc;

@@ -245,6 +245,23 @@ struct StreamDev {
     unsigned long long* local_proc; // [c * n_nodes] tau_v^(i), processor-major (REPT_FLAG_LOCAL_PER_PROCESSOR)
 };
 
+// The block a batch kernel's body runs as: its index among the nbx blocks that share one stream's
+// work (blockIdx.x and gridDim.x for a launch per stream, or a virtual block of the persistent group
+// kernel, which runs every step of the batch path for every stream of a group).
+struct Grid {
+    uint32_t bx, nbx;
+};
+
+// Grid-wide barrier state of the persistent group kernel (one per group, in device memory).  The
+// host clears count and timed_out before each launch and sets extra: the arrivals a barrier waits for
+// beyond the grid's blocks (0; a test sets 1 so that the wait can only run out).
+struct GroupSync {
+    unsigned int count;      // blocks arrived at the current barrier
+    unsigned int gen;        // barriers completed (advanced by the last block to arrive)
+    unsigned int timed_out;  // some block's wait gave up
+    unsigned int extra;
+};
+
 // One batch of edges appended to a stream.
 struct BatchDev {
     const uint32_t* src;
@@ -292,6 +309,19 @@ __device__ __forceinline__ uint64_t group_seed(uint64_t seed, uint32_t k) { retu
 __device__ __forceinline__ bool colour_is(uint32_t a, uint32_t b, uint64_t s_k, const FastMod& fm, uint32_t j) {
     uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
     return mod_equals_in_range(splitmix64(((lo << 32) | hi) ^ s_k), j, fm);
+}
+
+// Do the wedge edges {s, w} and {l, w} have the same colour in the group of seed s_k?  Their hash
+// values are congruent modulo m exactly when m divides their (exact, non-negative) difference, which
+// the divisibility test decides without a remainder; only then is the colour j itself formed.
+__device__ __forceinline__ bool same_colour(uint32_t s, uint32_t l, uint32_t w, uint64_t s_k, const FastMod& fm,
+                                            uint32_t& j) {
+    const uint64_t ks = ((uint64_t)(s < w ? s : w) << 32) | (s < w ? w : s);
+    const uint64_t kl = ((uint64_t)(l < w ? l : w) << 32) | (l < w ? w : l);
+    const uint64_t zs = splitmix64(ks ^ s_k), zl = splitmix64(kl ^ s_k);
+    if (!mod_equals_nobranch(zs >= zl ? zs - zl : zl - zs, 0u, fm)) return false;
+    j = fast_mod(zs, fm);
+    return true;
 }
 
 // Is edge {u, v} kept by some processor (k*m + h_k(u,v) < c for some group k)?

@@ -50,16 +50,16 @@ __device__ __forceinline__ bool table_insert(uint2* pool, unsigned long long bas
     return false;
 }
 
-__device__ __forceinline__ void k_classify_body(const StreamDev& d, const BatchDev& b) {
+__device__ __forceinline__ void k_classify_body(const StreamDev& d, const BatchDev& b, const Grid g) {
     // the previous batch's work list is consumed: clear the counting-sort histogram
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < kSortBuckets; i += gridDim.x * blockDim.x)
+    for (uint32_t i = g.bx * blockDim.x + threadIdx.x; i < kSortBuckets; i += g.nbx * blockDim.x)
         d.hist[i] = 0u;
-    if (blockIdx.x == 0 && threadIdx.x < kBins) d.ctrl->bin_next[threadIdx.x] = 0ull;
-    if (blockIdx.x == 0 && threadIdx.x == 0) d.ctrl->n_pairs = 0ull;
+    if (g.bx == 0 && threadIdx.x < kBins) d.ctrl->bin_next[threadIdx.x] = 0ull;
+    if (g.bx == 0 && threadIdx.x == 0) d.ctrl->n_pairs = 0ull;
     if (d.ctrl->status) return;
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < b.n;
+    const unsigned long long stride = (unsigned long long)g.nbx * blockDim.x;
+    for (unsigned long long base = (unsigned long long)g.bx * blockDim.x + threadIdx.x - lane; base < b.n;
          base += stride) {
         const unsigned long long e = base + lane;
         const bool valid = e < b.n;
@@ -79,12 +79,12 @@ __device__ __forceinline__ void k_classify_body(const StreamDev& d, const BatchD
     }
 }
 
-__device__ __forceinline__ void k_plan_body(const StreamDev& d) {
+__device__ __forceinline__ void k_plan_body(const StreamDev& d, const Grid g) {
     if (d.ctrl->status) return;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned long long n_t = d.ctrl->n_touched;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n_t;
+    const unsigned long long stride = (unsigned long long)g.nbx * blockDim.x;
+    for (unsigned long long base = (unsigned long long)g.bx * blockDim.x + threadIdx.x - lane; base < n_t;
          base += stride) {
         const unsigned long long i = base + lane;
         const bool valid = i < n_t;
@@ -142,15 +142,15 @@ constexpr uint32_t kBlockMoveSlots = 4096;
 // each, new tables of at most kMoveSlots slots) or k_rehash_huge (a thread block each).  meta[x].z
 // keeps the batch's new-entry count for k_insert, which counts it back down to zero; a batch that is not
 // applied clears it here.
-__device__ __forceinline__ void k_commit_body(const StreamDev& d) {
+__device__ __forceinline__ void k_commit_body(const StreamDev& d, const Grid g) {
     const unsigned status = d.ctrl->status;
     const unsigned long long n_t = d.ctrl->n_touched;
     const unsigned long long need = d.ctrl->need_quads, top = d.ctrl->pool_top;
     const bool bad = status != 0u || top + need > d.pool_quads;
-    if (status == 0u && bad && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&d.ctrl->status, kStCapacity);
+    if (status == 0u && bad && g.bx == 0 && threadIdx.x == 0) atomicOr(&d.ctrl->status, kStCapacity);
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n_t;
+    const unsigned long long stride = (unsigned long long)g.nbx * blockDim.x;
+    for (unsigned long long base = (unsigned long long)g.bx * blockDim.x + threadIdx.x - lane; base < n_t;
          base += stride) {
         const unsigned long long i = base + lane;
         bool defer = false, huge = false;
@@ -237,13 +237,15 @@ __device__ __forceinline__ bool move_block_smem(uint2* pool, uint32_t id_bits, b
 }
 
 // Move the blocks listed by k_commit whose new table has at most kMoveSlots slots: one warp per node.
-__device__ __forceinline__ void k_rehash_big_body(const StreamDev& d) {
-    __shared__ uint32_t s_keys[8][kMoveSlots];  // blocks of 256 threads
-    __shared__ uint32_t s_eidx[8][kMoveSlots];
+// `smem`: kMoveSmemWords words of shared memory (a key and a stream-index table of kMoveSlots slots
+// for each of the block's 8 warps).
+constexpr uint32_t kMoveSmemWords = 2u * 8u * kMoveSlots;
+static_assert(kMoveSmemWords >= 2u * kBlockMoveSlots, "the block move uses the same shared memory");
+__device__ __forceinline__ void k_rehash_big_body(const StreamDev& d, const Grid g, uint32_t* smem) {
     const unsigned long long n_big = d.ctrl->n_big, top = d.ctrl->pool_top;
     const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    for (unsigned long long k = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_big;
+    const unsigned long long warps = ((unsigned long long)g.nbx * blockDim.x) >> 5;
+    for (unsigned long long k = ((unsigned long long)g.bx * blockDim.x + threadIdx.x) >> 5; k < n_big;
          k += warps) {
         const uint32_t i = d.big[k];
         const uint32_t x = d.touched[i];
@@ -254,8 +256,8 @@ __device__ __forceinline__ void k_rehash_big_body(const StreamDev& d) {
         const uint32_t lg_new = table_lg(cnt_new);
         bool ok = true;
         if (fits && (1u << lg_new) <= kMoveSlots && REPT_CHECK(d.ctrl, 14, wid, 8u))
-            ok = move_block_smem<false>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, s_keys[wid],
-                                        s_eidx[wid], lane, 32u);
+            ok = move_block_smem<false>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new,
+                                        smem + wid * kMoveSlots, smem + (8u + wid) * kMoveSlots, lane, 32u);
         else if (fits)
             ok = move_block(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, lane, 32u);
         if (!ok) atomicOr(&d.ctrl->status, kStInternal);
@@ -266,9 +268,10 @@ __device__ __forceinline__ void k_rehash_big_body(const StreamDev& d) {
 
 // Move the blocks listed by k_commit whose new table has more than kMoveSlots slots: thread blocks
 // claim one node at a time, and build tables of at most kBlockMoveSlots slots in shared memory.
-__device__ __forceinline__ void k_rehash_huge_body(const StreamDev& d) {
-    __shared__ uint32_t s_keys[kBlockMoveSlots];
-    __shared__ uint32_t s_eidx[kBlockMoveSlots];
+// `smem`: kMoveSmemWords words of shared memory (a key and a stream-index table of kBlockMoveSlots slots).
+__device__ __forceinline__ void k_rehash_huge_body(const StreamDev& d, const Grid g, uint32_t* smem) {
+    uint32_t* s_keys = smem;
+    uint32_t* s_eidx = smem + kBlockMoveSlots;
     __shared__ unsigned long long s_k;
     __shared__ int s_bad;
     const unsigned long long n_huge = d.ctrl->n_huge, top = d.ctrl->pool_top;
@@ -303,10 +306,10 @@ __device__ __forceinline__ void k_rehash_huge_body(const StreamDev& d) {
     }
 }
 
-__device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev& b) {
+__device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev& b, const Grid g) {
     Ctrl* ct = d.ctrl;
     const unsigned status = ct->status;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (g.bx == 0 && threadIdx.x == 0) {
         // the batch's table space is now in use; reset the per-batch counters
         if (status == 0u) ct->pool_top += ct->need_quads;
         ct->need_quads = 0;
@@ -317,9 +320,9 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
     }
     if (status) return;
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    const unsigned long long stride = (unsigned long long)g.nbx * blockDim.x;
     unsigned long long n_loops = 0, n_kept = 0;  // this lane's tallies, added once per warp at the end
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < b.n;
+    for (unsigned long long base = (unsigned long long)g.bx * blockDim.x + threadIdx.x - lane; base < b.n;
          base += stride) {
         const unsigned long long e = base + lane;
         const bool valid = e < b.n;
@@ -405,12 +408,14 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
     }
 }
 
-// Exclusive scan of the counting-sort histogram (one block of 1024 threads): counts become the
-// first position of each key, and the class boundaries are recorded.  The counters are scanned in
-// chunks of 4096, thread t holding counters 4t..4t+3 of a chunk (one coalesced 16-byte load).
-__device__ __forceinline__ void k_sort_scan_body(const StreamDev& d) {
-    constexpr uint32_t kChunk = 4u * 1024u;
-    static_assert(kSortBuckets % kChunk == 0 && kKeyBuckets % kChunk == 0, "scan chunks");
+// Exclusive scan of the counting-sort histogram (one block of 256 or 1024 threads): counts become
+// the first position of each key, and the class boundaries are recorded.  The counters are scanned
+// in chunks of 4 * blockDim, thread t holding counters 4t..4t+3 of a chunk (one coalesced 16-byte
+// load); both block sizes divide the class size.
+__device__ __forceinline__ void k_sort_scan_body(const StreamDev& d, const Grid g) {
+    const uint32_t kChunk = 4u * blockDim.x;
+    static_assert(kKeyBuckets % 4096u == 0 && kSortBuckets % 4096u == 0, "scan chunks");
+    (void)g;
     __shared__ uint32_t warp_sum[33];
     if (d.ctrl->status) return;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
@@ -427,7 +432,7 @@ __device__ __forceinline__ void k_sort_scan_body(const StreamDev& d) {
         if (lane == 31) warp_sum[wid] = incl;
         __syncthreads();
         if (wid == 0) {
-            const uint32_t w = warp_sum[lane];
+            const uint32_t w = lane < (blockDim.x >> 5) ? warp_sum[lane] : 0u;
             uint32_t wi = w;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -463,11 +468,11 @@ __device__ __forceinline__ void k_sort_scan_body(const StreamDev& d) {
 }
 
 // Scatter each edge that can close a wedge to its place in the sorted work list.
-__device__ __forceinline__ void k_sort_scatter_body(const StreamDev& d, const BatchDev& b) {
+__device__ __forceinline__ void k_sort_scatter_body(const StreamDev& d, const BatchDev& b, const Grid g) {
     if (d.ctrl->status) return;
     const unsigned lane = threadIdx.x & 31u;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x - lane; base < b.n;
+    const unsigned long long stride = (unsigned long long)g.nbx * blockDim.x;
+    for (unsigned long long base = (unsigned long long)g.bx * blockDim.x + threadIdx.x - lane; base < b.n;
          base += stride) {
         const unsigned long long e = base + lane;
         WorkItem it{};
@@ -554,10 +559,8 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
     uint32_t found = 0, found2 = 0;
     uint32_t t_sw = kEmptyId, t_lw = kEmptyId;
     for (uint32_t k = d.kbeg; k < d.kend; ++k) {
-        const uint64_t sk = group_seed(d.seed, k);
-        const uint32_t js = colour_of(s, w, sk, d.fm);
-        uint32_t i;
-        if (processor_of(d, k, js, i) && colour_of(l, w, sk, d.fm) == js) {
+        uint32_t js, i;
+        if (same_colour(s, l, w, group_seed(d.seed, k), d.fm, js) && processor_of(d, k, js, i)) {
             atomicAdd(&s_proc[i], 1ull);
             if (d.local2 && k >= d.c1) ++found2; else ++found;
             if (d.local_proc) {
@@ -928,17 +931,18 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
 // class and find each item's stream from the prefix.  Closed wedges carry their stream in the
 // match queue and tau^(i) goes straight to global memory.
 
-// Per class c: pref[c * (k + 1) + i] = sum of the item counts of streams < i; cursors reset.
-__global__ void __launch_bounds__(1024) k_group_prefix(const StreamDev* __restrict__ ds, uint32_t k,
-                                                       unsigned long long* __restrict__ pref,
-                                                       unsigned long long* __restrict__ cursor) {
+// Per class c: pref[c * (k + 1) + i] = sum of the item counts of streams < i; cursors reset.  One
+// block of any multiple of 32 threads up to 1024.
+__device__ __forceinline__ void group_prefix_body(const StreamDev* __restrict__ ds, uint32_t k,
+                                                  unsigned long long* __restrict__ pref,
+                                                  unsigned long long* __restrict__ cursor) {
     __shared__ unsigned long long warp_sum[32];
     __shared__ unsigned long long carry;
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5, warps = blockDim.x >> 5;
     for (int c = 0; c < kBins; ++c) {
         if (tid == 0) carry = 0ull;
         __syncthreads();
-        for (uint32_t base = 0; base < k; base += 1024u) {
+        for (uint32_t base = 0; base < k; base += blockDim.x) {
             const uint32_t i = base + tid;
             const unsigned long long v = i < k && ds[i].ctrl->status == 0u ? ds[i].ctrl->bin_count[c] : 0ull;
             unsigned long long incl = v;
@@ -949,7 +953,7 @@ __global__ void __launch_bounds__(1024) k_group_prefix(const StreamDev* __restri
             if (lane == 31) warp_sum[wid] = incl;
             __syncthreads();
             if (wid == 0) {
-                const unsigned long long w = warp_sum[lane];
+                const unsigned long long w = lane < warps ? warp_sum[lane] : 0ull;
                 unsigned long long wi = w;
                 for (int o = 1; o < 32; o <<= 1) {
                     const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
@@ -961,7 +965,7 @@ __global__ void __launch_bounds__(1024) k_group_prefix(const StreamDev* __restri
             const unsigned long long excl = carry + warp_sum[wid] + incl - v;
             if (i < k) pref[c * (k + 1) + i] = excl;
             __syncthreads();
-            if (tid == 1023) carry = excl + v;
+            if (tid == blockDim.x - 1) carry = excl + v;
             __syncthreads();
         }
         if (tid == 0) {
@@ -970,6 +974,12 @@ __global__ void __launch_bounds__(1024) k_group_prefix(const StreamDev* __restri
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(1024) k_group_prefix(const StreamDev* __restrict__ ds, uint32_t k,
+                                                       unsigned long long* __restrict__ pref,
+                                                       unsigned long long* __restrict__ cursor) {
+    group_prefix_body(ds, k, pref, cursor);
 }
 
 struct GroupQueue {
@@ -988,10 +998,8 @@ __device__ __forceinline__ void gq_flush(const StreamDev* __restrict__ ds, Group
         const uint32_t s = q.s[i], l = q.l[i], w = q.w[i];
         uint32_t found = 0;
         for (uint32_t k = d.kbeg; k < d.kend; ++k) {
-            const uint64_t sk = group_seed(d.seed, k);
-            const uint32_t js = colour_of(s, w, sk, d.fm);
-            uint32_t i;
-            if (processor_of(d, k, js, i) && colour_of(l, w, sk, d.fm) == js) {
+            uint32_t js, i;
+            if (same_colour(s, l, w, group_seed(d.seed, k), d.fm, js) && processor_of(d, k, js, i)) {
                 ++found;
                 atomicAdd(&d.proc[i], 1ull);
             }
@@ -1113,14 +1121,17 @@ __device__ __forceinline__ void group_drain_warps(const StreamDev* __restrict__ 
     }
 }
 
-__global__ void __launch_bounds__(256, 4) k_intersect_group(const StreamDev* __restrict__ ds, uint32_t k,
-                                                            const unsigned long long* __restrict__ pref,
-                                                            unsigned long long* __restrict__ cursor) {
-    __shared__ uint32_t s_queue[256 / 32][kQueue];
-    __shared__ uint32_t s_match[256 / 32][4][kMatchQ];
+// Shared memory of the group intersection, per block of 8 warps: a key queue and a match queue of
+// four arrays (stream, s, l, w) per warp.
+constexpr uint32_t kGroupSmemWords = 8u * kQueue + 8u * 4u * kMatchQ;
+
+__device__ __forceinline__ void intersect_group_body(const StreamDev* __restrict__ ds, uint32_t k,
+                                                     const unsigned long long* __restrict__ pref,
+                                                     unsigned long long* __restrict__ cursor, uint32_t* smem) {
     const unsigned wid = threadIdx.x >> 5;
-    uint32_t* queue = s_queue[wid];
-    GroupQueue q{s_match[wid][0], s_match[wid][1], s_match[wid][2], s_match[wid][3], 0u};
+    uint32_t* queue = smem + wid * kQueue;
+    uint32_t* mq = smem + 8u * kQueue + wid * 4u * kMatchQ;
+    GroupQueue q{mq, mq + kMatchQ, mq + 2u * kMatchQ, mq + 3u * kMatchQ, 0u};
     group_drain_warps(ds, k, 5, kGrabHub, pref, cursor, queue, q);
     group_drain_warps(ds, k, 4, kGrabMid, pref, cursor, queue, q);
     group_drain_tiles<32>(ds, k, 3, pref, cursor, q);
@@ -1128,6 +1139,13 @@ __global__ void __launch_bounds__(256, 4) k_intersect_group(const StreamDev* __r
     group_drain_tiles<8>(ds, k, 1, pref, cursor, q);
     group_drain_tiles<4>(ds, k, 0, pref, cursor, q);
     if (q.n) gq_flush(ds, q, q.n);
+}
+
+__global__ void __launch_bounds__(256, 4) k_intersect_group(const StreamDev* __restrict__ ds, uint32_t k,
+                                                            const unsigned long long* __restrict__ pref,
+                                                            unsigned long long* __restrict__ cursor) {
+    __shared__ uint32_t smem[kGroupSmemWords];
+    intersect_group_body(ds, k, pref, cursor, smem);
 }
 
 // Algorithm 2's triangle-pair counters, folded in after the intersection.  Edge e of group k was a
@@ -1201,7 +1219,9 @@ __global__ void k_add_local(const unsigned long long* __restrict__ a, const unsi
 // Kernel entry points.  Each batch kernel exists twice: for one stream (state and batch passed by
 // value) and for many streams at once (`_multi`: blockIdx.y selects the stream, whose state and batch
 // descriptors are read from device arrays; blockIdx.x / gridDim.x then range over that stream's blocks).
-__global__ void k_classify(StreamDev d, BatchDev b) { k_classify_body(d, b); }
+__device__ __forceinline__ Grid launch_grid() { return Grid{blockIdx.x, gridDim.x}; }
+
+__global__ void k_classify(StreamDev d, BatchDev b) { k_classify_body(d, b, launch_grid()); }
 
 __global__ void k_classify_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
     __shared__ StreamDev sd;
@@ -1211,51 +1231,60 @@ __global__ void k_classify_multi(const StreamDev* __restrict__ ds, const BatchDe
         sb = bs[blockIdx.y];
     }
     __syncthreads();
-    k_classify_body(sd, sb);
+    k_classify_body(sd, sb, launch_grid());
 }
 
-__global__ void k_plan(StreamDev d) { k_plan_body(d); }
+__global__ void k_plan(StreamDev d) { k_plan_body(d, launch_grid()); }
 
 __global__ void k_plan_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
     (void)bs;
     __shared__ StreamDev sd;
     if (threadIdx.x == 0) sd = ds[blockIdx.y];
     __syncthreads();
-    k_plan_body(sd);
+    k_plan_body(sd, launch_grid());
 }
 
-__global__ void k_commit(StreamDev d) { k_commit_body(d); }
+__global__ void k_commit(StreamDev d) { k_commit_body(d, launch_grid()); }
 
 __global__ void k_commit_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
     (void)bs;
     __shared__ StreamDev sd;
     if (threadIdx.x == 0) sd = ds[blockIdx.y];
     __syncthreads();
-    k_commit_body(sd);
+    k_commit_body(sd, launch_grid());
 }
 
-__global__ void __launch_bounds__(256) k_rehash_big(StreamDev d) { k_rehash_big_body(d); }
+__global__ void __launch_bounds__(256) k_rehash_big(StreamDev d) {
+    __shared__ uint32_t smem[kMoveSmemWords];
+    k_rehash_big_body(d, launch_grid(), smem);
+}
 
 __global__ void __launch_bounds__(256) k_rehash_big_multi(const StreamDev* __restrict__ ds,
                                                             const BatchDev* __restrict__ bs) {
     (void)bs;
     __shared__ StreamDev sd;
+    __shared__ uint32_t smem[kMoveSmemWords];
     if (threadIdx.x == 0) sd = ds[blockIdx.y];
     __syncthreads();
-    k_rehash_big_body(sd);
+    k_rehash_big_body(sd, launch_grid(), smem);
 }
 
-__global__ void __launch_bounds__(1024) k_rehash_huge(StreamDev d) { k_rehash_huge_body(d); }
+__global__ void __launch_bounds__(1024) k_rehash_huge(StreamDev d) {
+    __shared__ uint32_t smem[kMoveSmemWords];
+    k_rehash_huge_body(d, launch_grid(), smem);
+}
 
-__global__ void __launch_bounds__(1024) k_rehash_huge_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
+__global__ void __launch_bounds__(1024) k_rehash_huge_multi(const StreamDev* __restrict__ ds,
+                                                              const BatchDev* __restrict__ bs) {
     (void)bs;
     __shared__ StreamDev sd;
+    __shared__ uint32_t smem[kMoveSmemWords];
     if (threadIdx.x == 0) sd = ds[blockIdx.y];
     __syncthreads();
-    k_rehash_huge_body(sd);
+    k_rehash_huge_body(sd, launch_grid(), smem);
 }
 
-__global__ void k_insert(StreamDev d, BatchDev b) { k_insert_body(d, b); }
+__global__ void k_insert(StreamDev d, BatchDev b) { k_insert_body(d, b, launch_grid()); }
 
 __global__ void k_insert_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
     __shared__ StreamDev sd;
@@ -1265,20 +1294,21 @@ __global__ void k_insert_multi(const StreamDev* __restrict__ ds, const BatchDev*
         sb = bs[blockIdx.y];
     }
     __syncthreads();
-    k_insert_body(sd, sb);
+    k_insert_body(sd, sb, launch_grid());
 }
 
-__global__ void __launch_bounds__(1024) k_sort_scan(StreamDev d) { k_sort_scan_body(d); }
+__global__ void __launch_bounds__(1024) k_sort_scan(StreamDev d) { k_sort_scan_body(d, launch_grid()); }
 
-__global__ void __launch_bounds__(1024) k_sort_scan_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
+__global__ void __launch_bounds__(1024) k_sort_scan_multi(const StreamDev* __restrict__ ds,
+                                                           const BatchDev* __restrict__ bs) {
     (void)bs;
     __shared__ StreamDev sd;
     if (threadIdx.x == 0) sd = ds[blockIdx.y];
     __syncthreads();
-    k_sort_scan_body(sd);
+    k_sort_scan_body(sd, launch_grid());
 }
 
-__global__ void k_sort_scatter(StreamDev d, BatchDev b) { k_sort_scatter_body(d, b); }
+__global__ void k_sort_scatter(StreamDev d, BatchDev b) { k_sort_scatter_body(d, b, launch_grid()); }
 
 __global__ void k_sort_scatter_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
     __shared__ StreamDev sd;
@@ -1288,7 +1318,121 @@ __global__ void k_sort_scatter_multi(const StreamDev* __restrict__ ds, const Bat
         sb = bs[blockIdx.y];
     }
     __syncthreads();
-    k_sort_scatter_body(sd, sb);
+    k_sort_scatter_body(sd, sb, launch_grid());
+}
+
+// ---------------------------------------------------------------------------------------------
+// One persistent launch for a whole group round: every step of the batch path (classify, plan,
+// commit, both block moves, insert, sort, the group's intersection) for every stream, separated by
+// grid-wide barriers.  The grid is co-resident (a cooperative launch); each step runs over virtual
+// blocks (stream, block of that stream) exactly as the launch per step would, so the counts are the
+// same.  Every barrier wait is bounded in time: when it runs out, the block records kStTimeout in
+// every stream's status (REPT_E_TIMEOUT at the next synchronising call) and returns, and the other
+// blocks, seeing timed_out, stop waiting and return too.  No block ever waits without a limit.
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// All blocks of the grid meet; false if the wait gave up (after wait_ns nanoseconds) or another
+// block's did.
+__device__ __forceinline__ bool grid_barrier(GroupSync* gs, unsigned long long wait_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = &gs->gen;
+        volatile unsigned int* vto = &gs->timed_out;
+        int ok = 1;
+        const unsigned int g = *vgen;  // cannot advance before this block arrives
+        __threadfence();               // this block's writes of the step before the barrier
+        const unsigned int target = gridDim.x + gs->extra;
+        if (atomicAdd(&gs->count, 1u) == target - 1u) {
+            atomicExch(&gs->count, 0u);
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*vgen == g) {
+                if (*vto || global_ns() - t0 > wait_ns) {
+                    atomicExch(&gs->timed_out, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Virtual blocks per stream of each step (the multi-launch shape's grid x dimensions).
+struct PersistShape {
+    uint32_t x_edge, x_big, x_huge;
+};
+
+// Dynamic shared memory of the persistent kernel: the larger of the block moves' and the group
+// intersection's needs.
+constexpr uint32_t kPersistSmemWords = kMoveSmemWords > kGroupSmemWords ? kMoveSmemWords : kGroupSmemWords;
+
+__global__ void __launch_bounds__(256, 3) k_group_persistent(const StreamDev* __restrict__ ds,
+                                                           const BatchDev* __restrict__ bs, uint32_t k,
+                                                           PersistShape sh, unsigned long long* __restrict__ pref,
+                                                           unsigned long long* __restrict__ cursor, GroupSync* gs,
+                                                           unsigned long long wait_ns) {
+    extern __shared__ __align__(16) uint32_t psmem[];
+    __shared__ StreamDev sd;
+    __shared__ BatchDev sb;
+    __shared__ uint32_t s_cur;
+    if (threadIdx.x == 0) s_cur = 0xFFFFFFFFu;
+    __syncthreads();
+    // run `body` for every virtual block (stream, block x of X) this block is dealt
+    auto step = [&](uint32_t X, auto&& body) {
+        const unsigned long long total = (unsigned long long)k * X;
+        for (unsigned long long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+            const uint32_t sid = (uint32_t)(vb / X);
+            if (sid != s_cur) {  // uniform over the block
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    sd = ds[sid];
+                    sb = bs[sid];
+                    s_cur = sid;
+                }
+                __syncthreads();
+            }
+            body(Grid{(uint32_t)(vb % X), X});
+        }
+    };
+    bool ok = true;
+    step(sh.x_edge, [&](Grid g) { k_classify_body(sd, sb, g); });
+    ok = ok && grid_barrier(gs, wait_ns);
+    if (ok) step(sh.x_edge, [&](Grid g) { k_plan_body(sd, g); });
+    ok = ok && grid_barrier(gs, wait_ns);
+    if (ok) step(sh.x_edge, [&](Grid g) { k_commit_body(sd, g); });
+    ok = ok && grid_barrier(gs, wait_ns);
+    if (ok) step(sh.x_big, [&](Grid g) { k_rehash_big_body(sd, g, psmem); });
+    ok = ok && grid_barrier(gs, wait_ns);
+    if (ok) step(sh.x_huge, [&](Grid g) { k_rehash_huge_body(sd, g, psmem); });
+    ok = ok && grid_barrier(gs, wait_ns);
+    if (ok) step(sh.x_edge, [&](Grid g) { k_insert_body(sd, sb, g); });
+    ok = ok && grid_barrier(gs, wait_ns);
+    if (ok) step(1u, [&](Grid g) { k_sort_scan_body(sd, g); });
+    ok = ok && grid_barrier(gs, wait_ns);
+    if (ok) step(sh.x_edge, [&](Grid g) { k_sort_scatter_body(sd, sb, g); });
+    ok = ok && grid_barrier(gs, wait_ns);
+    if (ok && blockIdx.x == 0) group_prefix_body(ds, k, pref, cursor);
+    ok = ok && grid_barrier(gs, wait_ns);
+    if (ok) {
+        intersect_group_body(ds, k, pref, cursor, psmem);
+        return;
+    }
+    // a wait ran out: the round is not applied for any stream (every step checks the status first)
+    if (threadIdx.x == 0)
+        for (uint32_t i = blockIdx.x; i < k; i += gridDim.x) atomicOr(&ds[i].ctrl->status, kStTimeout);
 }
 
 // Streams whose entries carry their colour (one hash group, m <= 256): 5 blocks of 256 threads per SM.

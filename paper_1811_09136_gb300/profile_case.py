@@ -2,12 +2,15 @@
 
   python -m paper_1811_09136_gb300.profile_case --workload rmat_s20 --m 100 --c 100
   python -m paper_1811_09136_gb300.profile_case --chung-lu 1048576 2.1 16777216 50000 --m 20 --c 100
+  python -m paper_1811_09136_gb300.profile_case --mix 32 --batch 1048576 --mode group
 
 The stream is ingested once in batches of --batch edges into a handle whose pool grows as needed, so
 that the device holds little beyond the state the stream needs.  Kernel launches per batch follow
 the library's launch order (classify, plan, commit, two block-move kernels, insert, two sort
-kernels, intersect), which is what a profiler's launch skip count (-s) refers to.  With --group K
-the same stream is fed as K streams with distinct hash seeds through one rept_group instead.
+kernels, intersect), which is what a profiler's launch skip count (-s) refers to.  With --mix N the
+first N streams of the batched workload's mix (seed 1000) are counted instead, each with its own
+m = c and hash seed, through one rept_group (--mode group: one launch per step for all streams;
+persistent: one cooperative launch per round) or one stream after the other (--mode plain).
 """
 from __future__ import annotations
 
@@ -25,10 +28,26 @@ def main():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--batch", type=int, default=1 << 20)
     ap.add_argument("--work", action="store_true", help="with work counters (REPT_FLAG_WORK_COUNTERS)")
+    ap.add_argument("--mix", type=int, default=0, help="count the first N streams of the batched mix instead")
+    ap.add_argument("--mode", default="group", choices=["group", "persistent", "plain"])
     args = ap.parse_args()
 
     import torch
     from . import graphgen, rept
+
+    if args.mix:
+        from . import batched
+        specs = batched.mix_specs(args.mix, seed=1000)
+        streams = batched.generate_all(specs)
+        params = [(sp.m, sp.m, sp.hash_seed) for sp in specs]
+        if args.mode == "plain":
+            res, t = batched.run_plain(streams, params, batch=args.batch)
+        else:
+            res, t = batched.run_batched(streams, params, batch=args.batch, graph=False,
+                                         persistent=args.mode == "persistent")
+        print(f"{sum(len(x) for x in streams)} edges in {len(streams)} streams, "
+              f"{sum(int(r.proc.sum()) for r in res)} semi-triangles, {t:.3f} s", flush=True)
+        return
 
     if args.chung_lu:
         n, gamma, e, cap = args.chung_lu

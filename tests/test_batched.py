@@ -43,11 +43,15 @@ def _mix(k=7, seed=31):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("graph,presize,batch", [(True, True, 1 << 12), (False, True, 777), (True, False, 1 << 10)])
-def test_batched_equals_plain_and_oracle(graph, presize, batch):
+@pytest.mark.parametrize("graph,presize,batch,persistent", [(True, True, 1 << 12, False), (False, True, 777, False),
+                                                            (True, False, 1 << 10, False), (False, True, 1 << 11, True),
+                                                            (True, True, 999, True), (True, False, 1 << 10, True)])
+def test_batched_equals_plain_and_oracle(graph, presize, batch, persistent):
+    """Launch per step, with and without graphs, pools presized or grown, and one persistent launch per
+    round (REPT_GROUP_PERSISTENT; with pools that may grow a round falls back to the launch per step)."""
     streams, params = _mix()
     res_b, _ = batched.run_batched(streams, params, batch=batch, graph=graph, presize=presize,
-                                   local_estimates=True)
+                                   local_estimates=True, persistent=persistent)
     res_p, _ = batched.run_plain(streams, params, batch=batch, local_estimates=True)
     for s, (m, c, seed), rb, rp in zip(streams, params, res_b, res_p):
         ref = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, seed, pair_counters=False)
@@ -151,3 +155,51 @@ def test_batched_midsize_stream_runs_the_hub_classes_and_matches_the_oracle():
             assert np.array_equal(r.proc, ref.tau_proc)
             assert np.array_equal(r.local, ref.local1)
             assert abs(r.tau_hat - ref_g) <= 1e-12 * max(abs(ref_g), 1.0)
+
+
+@pytest.mark.gpu
+def test_persistent_wait_that_runs_out_reports_timeout_and_leaves_the_device_usable():
+    """The test hook REPT_GROUP_TEST_TIMEOUT makes the persistent kernel's first grid-wide wait expect
+    one block more than the grid holds, so every block's wait runs out after 0.1 s: the kernel records
+    the timeout and returns (no block waits without a limit), each stream reports REPT_E_TIMEOUT with
+    nothing applied, and after rept_reset the same handles count the oracle's values."""
+    import torch
+    from paper_1811_09136_gb300 import rept
+    streams, params = _mix(k=3, seed=71)
+    dev = [(torch.from_numpy(s.src.view(np.int32)).cuda(), torch.from_numpy(s.dst.view(np.int32)).cuda())
+           for s in streams]
+    handles = [rept.ReptStream(s.n_nodes, m, c, seed, expected_edges=len(s), max_batch=len(s))
+               for s, (m, c, seed) in zip(streams, params)]
+    try:
+        bad = batched.ReptGroup(len(handles), graph=False, persistent=True, test_timeout=True)
+        bad.ingest(handles, [d[0] for d in dev], [d[1] for d in dev])
+        for h in handles:
+            proc, _, rc = h.counts(allow_error=True)
+            assert rc == -6, rc                        # REPT_E_TIMEOUT
+            assert int(proc.sum()) == 0                # the round was not applied
+        bad.close()
+        torch.cuda.synchronize()                       # the context is still usable
+        good = batched.ReptGroup(len(handles), graph=False, persistent=True)
+        for h in handles:
+            h.reset()
+        good.ingest(handles, [d[0] for d in dev], [d[1] for d in dev])
+        for h, s, (m, c, seed) in zip(handles, streams, params):
+            proc, local = h.counts()
+            ref = O.rept_stream(s.src, s.dst, s.n_nodes, m, c, seed, pair_counters=False)
+            assert np.array_equal(proc, ref.tau_proc)
+            assert np.array_equal(local.cpu().numpy().view(np.uint64), ref.local1)
+        good.close()
+    finally:
+        for h in handles:
+            h.close()
+
+
+def test_timeout_hook_needs_the_persistent_flag():
+    """REPT_GROUP_TEST_TIMEOUT alone is refused before any device work (no GPU needed)."""
+    import ctypes
+    from paper_1811_09136_gb300 import rept
+    lib = rept.load()
+    lib.rept_group_create.restype = ctypes.c_int
+    lib.rept_group_create.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]
+    h = ctypes.c_void_p()
+    assert lib.rept_group_create(4, batched.GROUP_TEST_TIMEOUT, ctypes.byref(h)) == -1
