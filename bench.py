@@ -361,7 +361,7 @@ def single_leg(name, m, c, seed, steps, warmup, dev, pg, digests, clock_mhz_hint
     k3_s = k3_ms / steps * 1e-3
     hbm, hbm_src = peaks()
     achieved = k3_bytes / k3_s / 1e9
-    ws_bytes = 8 * T + 8 * st["pool_used"] + 24 * s.n_nodes
+    ws_bytes = 8 * T + 8 * st["pool_used"] + 28 * s.n_nodes
     out = {
         "edges": T, "value": world * steps * T / (ms_max * 1e-3), "unit": "edges/s", "steps": steps,
         "warmup": warmup, "ms_per_step": ms_max / steps, "tau_hat": g, "semi_triangles": int(proc.sum()),

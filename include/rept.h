@@ -349,8 +349,8 @@ int rept_ingest_multi(rept_state* const* hs, const uint32_t* const* d_src, const
  * control block) lives in one statically allocated device array of
  * REPT_NOALLOC_SCRATCH_BYTES (64 MiB) inside this library; every GPU that
  * loads the library holds that array until the process exits.  A problem
- * needs 16 * n_nodes + 216 * n_edges + 200 KiB bytes of it (for example
- * 2^20 nodes and 230,000 edges); larger problems return REPT_E_SCRATCH
+ * needs 20 * n_nodes + 216 * n_edges + 200 KiB bytes of it (for example
+ * 2^20 nodes and 210,000 edges); larger problems return REPT_E_SCRATCH
  * before any device work is enqueued.  c must be at most 4096.
  *
  * Arguments: d_src / d_dst: device arrays of n_edges uint32 endpoints

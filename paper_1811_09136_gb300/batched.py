@@ -161,7 +161,7 @@ class StreamResult:
 def _state_bytes(n_nodes: int, edges: int, batch: int) -> int:
     """Device bytes a stream's state needs: per-node arrays, per-batch scratch, and the pool at the
     guaranteed bound (32 slots of 8 bytes per edge)."""
-    return 24 * n_nodes + 200_000 + 96 * batch + 256 * edges + (1 << 20)
+    return 28 * n_nodes + 200_000 + 96 * batch + 256 * edges + (1 << 20)
 
 
 def _waves(streams, batch, budget):

@@ -392,6 +392,7 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     unsigned long long quads = quads_bound(cfg->expected_edges ? cfg->expected_edges : mb, words);
     if (quads > 0xFFFFFFFFull) quads = 0xFFFFFFFFull;
     if ((rc = dev_alloc(s, (void**)&d.meta, (size_t)n * sizeof(uint4)))) return fail(rc);
+    if ((rc = dev_alloc(s, (void**)&d.cnt_add, (size_t)n * sizeof(uint32_t)))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&d.local, (size_t)n * sizeof(unsigned long long)))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&d.proc, (size_t)cfg->c * sizeof(unsigned long long)))) return fail(rc);
     if ((rc = dev_alloc(s, (void**)&d.ctrl, sizeof(Ctrl)))) return fail(rc);
@@ -446,6 +447,7 @@ int rept_reset(rept_state* s, void* stream) {
     if (used > d.pool_quads) used = d.pool_quads;
     if (used) REPT_CUDA(cudaMemsetAsync(d.pool, 0xFF, used * 32ull, st));
     REPT_CUDA(cudaMemsetAsync(d.meta, 0, n * sizeof(uint4), st));
+    REPT_CUDA(cudaMemsetAsync(d.cnt_add, 0, n * sizeof(uint32_t), st));
     REPT_CUDA(cudaMemsetAsync(d.local, 0, n * sizeof(unsigned long long), st));
     REPT_CUDA(cudaMemsetAsync(d.proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
     if (d.local2) REPT_CUDA(cudaMemsetAsync(d.local2, 0, n * sizeof(unsigned long long), st));
@@ -472,6 +474,7 @@ int rept_reset_async(rept_state* s, uint64_t seed, void* stream) {
     const size_t n = d.n_nodes;
     REPT_CUDA(cudaMemsetAsync(d.pool, 0xFF, d.pool_quads * 32ull, st));
     REPT_CUDA(cudaMemsetAsync(d.meta, 0, n * sizeof(uint4), st));
+    REPT_CUDA(cudaMemsetAsync(d.cnt_add, 0, n * sizeof(uint32_t), st));
     REPT_CUDA(cudaMemsetAsync(d.local, 0, n * sizeof(unsigned long long), st));
     REPT_CUDA(cudaMemsetAsync(d.proc, 0, (size_t)d.c * sizeof(unsigned long long), st));
     if (d.local2) REPT_CUDA(cudaMemsetAsync(d.local2, 0, n * sizeof(unsigned long long), st));
@@ -792,6 +795,7 @@ void rept_destroy(rept_state* s) {
     cudaDeviceSynchronize();
     StreamDev& d = s->d;
     cudaFree(d.meta);
+    cudaFree(d.cnt_add);
     cudaFree(d.local);
     cudaFree(d.proc);
     cudaFree(d.ctrl);

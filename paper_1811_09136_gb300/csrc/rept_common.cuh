@@ -8,7 +8,9 @@
 //                   boundary.  add counts the current batch's new entries of x
 //                   (zero between batches); it shares x's 16-byte record so
 //                   that the insert's position counter and the block's place
-//                   sit in one 32-byte sector.
+//                   sit in one 32-byte sector.  k_classify counts into the
+//                   compact array cnt_add[n_nodes] first; k_plan moves the
+//                   counts into the records.
 //   pool[]          8-byte slots: per node, an open-addressing (linear probing,
 //                   4-key buckets) table of 2^lg neighbour ids with a parallel
 //                   array of their stream indices (2^lg slots in all), then
@@ -204,6 +206,9 @@ struct StreamDev {
     FastMod fm;         // x mod m
     uint32_t tile_max;  // edges whose smaller endpoint has more entries get a warp (4, 8, 16 or 32)
     uint4* meta;  // per node {block offset in 4-slot units, entries, this batch's new entries, 0}
+    uint32_t* cnt_add;  // [n_nodes] new entries per node as k_classify counts them (a compact array, so
+                        // that its atomics stay in L2); k_plan moves each touched node's count into its
+                        // record and clears it, so it is zero between batches
     uint2* pool;
     unsigned long long pool_quads;
     // How list entries carry their edge's colours (the intersection tests colours before it probes):
@@ -355,10 +360,13 @@ __host__ __device__ __forceinline__ bool has_words(const StreamDev& d) { return 
 // 1/m of the probes are skipped.
 __device__ __forceinline__ bool wedge_may_count(const StreamDev& d, uint32_t l, uint32_t w, uint32_t js) {
     // every step evaluated and combined with & (no early exit), so the lanes of a warp never part
-    // ways over it (measured 4 % faster than the short-circuit form)
+    // ways over it (measured 4 % faster than the short-circuit form).  With one hash group the
+    // processor of colour js is js itself: REPT keeps every colour below m (and js < m), parallel
+    // MASCOT's single sampler keeps colour 0 only (pbeg = 0, pcount = 1), so the shard's range test
+    // alone decides processor_of here.
     const uint64_t lo = l < w ? l : w, hi = l < w ? w : l;
     const uint64_t z = splitmix64(((lo << 32) | hi) ^ d.seed);
-    return (js < d.keep) & (js - d.pbeg < d.pcount) & mod_equals_nobranch(z, js, d.fm);
+    return (js - d.pbeg < d.pcount) & mod_equals_nobranch(z, js, d.fm);
 }
 
 // With several hash groups (kColWords), a wedge (s, w), (l, w) can count only for a group k whose

@@ -70,8 +70,8 @@ __device__ __forceinline__ void k_classify_body(const StreamDev& d, const BatchD
         const bool kept = valid && in_range && u != v && kept_by_any(d, u, v);
         bool first_u = false, first_v = false;
         if (kept) {
-            first_u = atomicAdd(&d.meta[u].z, 1u) == 0u;
-            first_v = atomicAdd(&d.meta[v].z, 1u) == 0u;
+            first_u = atomicAdd(&d.cnt_add[u], 1u) == 0u;
+            first_v = atomicAdd(&d.cnt_add[v], 1u) == 0u;
         }
         unsigned long long o = warp_reserve(&d.ctrl->n_touched, (unsigned)first_u + (unsigned)first_v);
         if (first_u) d.touched[o++] = u;
@@ -91,8 +91,9 @@ __device__ __forceinline__ void k_plan_body(const StreamDev& d, const Grid g) {
         unsigned long long need = 0;
         if (valid) {
             const uint32_t x = d.touched[i];
-            const uint4 mx = d.meta[x];
-            const uint32_t cnt = mx.y, add = mx.z;
+            const uint32_t cnt = d.meta[x].y, add = d.cnt_add[x];
+            d.cnt_add[x] = 0u;     // zero again for the next batch
+            d.meta[x].z = add;     // the count travels with the node's record from here on
             const uint32_t lg_old = table_lg(cnt), lg_new = table_lg(cnt + add);
             if (lg_new != lg_old) need = block_quads(lg_new, has_words(d));
         }
@@ -553,6 +554,10 @@ __device__ __forceinline__ void pair_event(const StreamDev& d, uint32_t t, uint3
     if (atomicAdd(&d.pair_evt[idx], 1u) == 0u) d.pair_list[atomicAdd(&d.ctrl->n_pairs, 1ull)] = (uint32_t)idx;
 }
 
+// DIFF: decide each group's colour agreement from the two hash values' difference (same_colour: one
+// remainder only when they agree), which pays where wedges are counted under several groups (the
+// probe variant); the single-group variants form both colours, which keeps their registers lower.
+template <bool DIFF>
 __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, uint32_t l, uint32_t w,
                                                 unsigned long long* s_proc) {
     if (!REPT_CHECK(d.ctrl, 9, max(w, max(s, l)), d.n_nodes)) return 0u;
@@ -560,7 +565,15 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
     uint32_t t_sw = kEmptyId, t_lw = kEmptyId;
     for (uint32_t k = d.kbeg; k < d.kend; ++k) {
         uint32_t js, i;
-        if (same_colour(s, l, w, group_seed(d.seed, k), d.fm, js) && processor_of(d, k, js, i)) {
+        bool agree;
+        if (DIFF) {
+            agree = same_colour(s, l, w, group_seed(d.seed, k), d.fm, js) && processor_of(d, k, js, i);
+        } else {
+            const uint64_t sk = group_seed(d.seed, k);
+            js = colour_of(s, w, sk, d.fm);
+            agree = processor_of(d, k, js, i) && colour_of(l, w, sk, d.fm) == js;
+        }
+        if (agree) {
             atomicAdd(&s_proc[i], 1ull);
             if (d.local2 && k >= d.c1) ++found2; else ++found;
             if (d.local_proc) {
@@ -604,20 +617,20 @@ struct MatchQueue {
     uint32_t n;
 };
 
-template <bool WORK>
+template <bool WORK, bool DIFF>
 __device__ __forceinline__ void mq_flush(const StreamDev& d, MatchQueue& q, uint32_t take,
                                          unsigned long long* s_proc, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     if (lane < take) {
         const uint32_t i = q.n - take + lane;
-        const uint32_t f = count_wedge(d, q.s[i], q.l[i], q.w[i], s_proc);
+        const uint32_t f = count_wedge<DIFF>(d, q.s[i], q.l[i], q.w[i], s_proc);
         if (WORK) wk.counted += f;
     }
     q.n -= take;
     __syncwarp();
 }
 
-template <bool WORK>
+template <bool WORK, bool DIFF>
 __device__ __forceinline__ void mq_push(const StreamDev& d, MatchQueue& q, bool has, uint32_t s, uint32_t l,
                                         uint32_t w, unsigned long long* s_proc, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
@@ -632,12 +645,12 @@ __device__ __forceinline__ void mq_push(const StreamDev& d, MatchQueue& q, bool 
     }
     q.n += __popc(mask);
     __syncwarp();
-    if (q.n >= 32u) mq_flush<WORK>(d, q, 32u, s_proc, wk);
+    if (q.n >= 32u) mq_flush<WORK, DIFF>(d, q, 32u, s_proc, wk);
 }
 
 // Edges whose smaller endpoint has at most TILE entries: one tile of TILE lanes per edge, one list
 // entry per lane.
-template <int TILE, bool WORK>
+template <int TILE, bool WORK, bool DIFF>
 __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkItem& x, bool valid,
                                                unsigned long long* s_proc, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u, j = lane & (TILE - 1);
@@ -661,7 +674,7 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
             w = ws;
         }
     }
-    mq_push<WORK>(d, mq, has, x.s, x.l, w, s_proc, wk);
+    mq_push<WORK, DIFF>(d, mq, has, x.s, x.l, w, s_proc, wk);
 }
 
 // Edges whose smaller endpoint has more entries: a warp per edge.  Each pass reads 128 entries of
@@ -806,7 +819,7 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
     }
 }
 
-template <int TILE, bool WORK>
+template <int TILE, bool WORK, bool DIFF>
 __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, int cls, unsigned long long* s_proc,
                                                MatchQueue& mq, Work& wk) {
     constexpr uint32_t kPerWarp = 32 / TILE, kRounds = 4, kGrab = kPerWarp * kRounds;
@@ -824,7 +837,7 @@ __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, int cls, unsi
             const bool valid = i < count;
             WorkItem x{};
             if (valid) x = items[i];
-            intersect_tile<TILE, WORK>(d, x, valid, s_proc, mq, wk);
+            intersect_tile<TILE, WORK, DIFF>(d, x, valid, s_proc, mq, wk);
         }
     }
 }
@@ -846,7 +859,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint
         for (unsigned long long i = i0; i < i1; ++i) {
             const WorkItem x = items[i];
             intersect_warp<WORK, MODE>(d, x, queue, wk, [&](bool has, uint32_t w) {
-                mq_push<WORK>(d, mq, has, x.s, x.l, w, s_proc, wk);
+                mq_push<WORK, MODE == (int)kColNone>(d, mq, has, x.s, x.l, w, s_proc, wk);
             });
         }
     }
@@ -889,15 +902,15 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
         mark(5);
         drain_warp_bin<WORK, MODE>(d, 4, kGrabMid, s_proc, queue, mq, wk);
         mark(4);
-        drain_tile_bin<32, WORK>(d, 3, s_proc, mq, wk);
+        drain_tile_bin<32, WORK, MODE == (int)kColNone>(d, 3, s_proc, mq, wk);
         mark(3);
-        drain_tile_bin<16, WORK>(d, 2, s_proc, mq, wk);
+        drain_tile_bin<16, WORK, MODE == (int)kColNone>(d, 2, s_proc, mq, wk);
         mark(2);
-        drain_tile_bin<8, WORK>(d, 1, s_proc, mq, wk);
+        drain_tile_bin<8, WORK, MODE == (int)kColNone>(d, 1, s_proc, mq, wk);
         mark(1);
-        drain_tile_bin<4, WORK>(d, 0, s_proc, mq, wk);
+        drain_tile_bin<4, WORK, MODE == (int)kColNone>(d, 0, s_proc, mq, wk);
         mark(0);
-        if (mq.n) mq_flush<WORK>(d, mq, mq.n, s_proc, wk);
+        if (mq.n) mq_flush<WORK, MODE == (int)kColNone>(d, mq, mq.n, s_proc, wk);
         if (WORK && blockIdx.x == 0 && threadIdx.x < kBins)
             d.ctrl->class_items[threadIdx.x] += d.ctrl->bin_count[threadIdx.x];
     }
@@ -998,8 +1011,10 @@ __device__ __forceinline__ void gq_flush(const StreamDev* __restrict__ ds, Group
         const uint32_t s = q.s[i], l = q.l[i], w = q.w[i];
         uint32_t found = 0;
         for (uint32_t k = d.kbeg; k < d.kend; ++k) {
-            uint32_t js, i;
-            if (same_colour(s, l, w, group_seed(d.seed, k), d.fm, js) && processor_of(d, k, js, i)) {
+            const uint64_t sk = group_seed(d.seed, k);
+            const uint32_t js = colour_of(s, w, sk, d.fm);
+            uint32_t i;
+            if (processor_of(d, k, js, i) && colour_of(l, w, sk, d.fm) == js) {
                 ++found;
                 atomicAdd(&d.proc[i], 1ull);
             }

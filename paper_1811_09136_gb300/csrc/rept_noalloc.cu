@@ -25,7 +25,7 @@ inline unsigned long long align256(unsigned long long x) { return (x + 255ull) &
 
 // Offsets of the state inside the scratch area for n nodes and E edges.
 struct Layout {
-    unsigned long long meta, touched, grow_rel, big, rec, srec, hist, ctrl, pool, end;
+    unsigned long long meta, cnt_add, touched, grow_rel, big, rec, srec, hist, ctrl, pool, end;
     unsigned long long pool_quads;
 };
 
@@ -33,6 +33,7 @@ Layout layout_for(unsigned long long n, unsigned long long E) {
     Layout L{};
     unsigned long long o = 0;
     L.meta = o;     o = align256(o + n * sizeof(uint4));
+    L.cnt_add = o;  o = align256(o + n * sizeof(uint32_t));
     L.touched = o;  o = align256(o + 2 * E * sizeof(uint32_t));
     L.grow_rel = o; o = align256(o + 2 * E * sizeof(uint32_t));
     L.big = o;      o = align256(o + 2 * E * sizeof(uint32_t));
@@ -116,6 +117,7 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
     d.fm = make_fastmod(m);
     d.tile_max = 32u;
     d.meta = reinterpret_cast<uint4*>(sc + L.meta);
+    d.cnt_add = reinterpret_cast<uint32_t*>(sc + L.cnt_add);
     d.touched = reinterpret_cast<uint32_t*>(sc + L.touched);
     d.grow_rel = reinterpret_cast<uint32_t*>(sc + L.grow_rel);
     d.big = reinterpret_cast<uint32_t*>(sc + L.big);
@@ -131,6 +133,7 @@ extern "C" int rept_count_noalloc(const uint32_t* d_src, const uint32_t* d_dst, 
 
     // the scratch keeps the previous call's contents: clear what must start empty
     NA_CUDA(cudaMemsetAsync(d.meta, 0, (size_t)n_nodes * sizeof(uint4), st));
+    NA_CUDA(cudaMemsetAsync(d.cnt_add, 0, (size_t)n_nodes * sizeof(uint32_t), st));
     NA_CUDA(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), st));
     NA_CUDA(cudaMemsetAsync(d.pool, 0xFF, L.pool_quads * 32ull, st));
     NA_CUDA(cudaMemsetAsync(d_proc, 0, (size_t)c * sizeof(uint64_t), st));

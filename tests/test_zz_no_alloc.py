@@ -86,7 +86,7 @@ def test_noalloc_matches_regular_entry_points_on_two_calls_in_a_row():
 def test_noalloc_rejects_problems_beyond_its_scratch():
     import torch
     fn = _lib()
-    n, E = 1 << 22, 1 << 20  # 16 n + 216 E + 200 KiB > 64 MiB
+    n, E = 1 << 22, 1 << 20  # 20 n + 216 E + 200 KiB > 64 MiB
     src = torch.zeros(E, dtype=torch.int32, device="cuda")
     out = torch.zeros(n, dtype=torch.int64, device="cuda")
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
