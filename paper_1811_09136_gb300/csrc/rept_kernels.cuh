@@ -756,6 +756,7 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
         if (PREFETCH && j0 + 128u < n_s) load_pass(j0 + 128u);
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
+            if (j0 + 64u * half >= n_s) break;  // an empty half (short lists, last passes): uniform skip
             const uint32_t jj = j0 + 64u * half + 2u * lane;
             const uint4 q = cq[half];
             const uint32_t w1 = q.x & mask, w2 = q.z & mask;

@@ -27,7 +27,8 @@ def main():
     ap.add_argument("--c", type=int, default=100)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--batch", type=int, default=1 << 20)
-    ap.add_argument("--work", action="store_true", help="with work counters (REPT_FLAG_WORK_COUNTERS)")
+    ap.add_argument("--work", action="store_true",
+                    help="with work counters (REPT_FLAG_WORK_COUNTERS), printing each batch's scanned entries")
     ap.add_argument("--mix", type=int, default=0, help="count the first N streams of the batched mix instead")
     ap.add_argument("--mode", default="group", choices=["group", "persistent", "plain"])
     args = ap.parse_args()
@@ -58,8 +59,13 @@ def main():
     dst = torch.from_numpy(s.dst.view(np.int32)).cuda()
     flags = rept.FLAG_WORK_COUNTERS if args.work else 0
     with rept.ReptStream(s.n_nodes, args.m, args.c, args.seed, max_batch=args.batch, flags=flags) as r:
-        for off in range(0, len(s), args.batch):
+        prev = 0
+        for b, off in enumerate(range(0, len(s), args.batch)):
             r.ingest(src[off:off + args.batch], dst[off:off + args.batch])
+            if args.work:  # the intersection's scanned entries of this batch (one launch)
+                st = r.stats()
+                print(f"batch {b}: {st['small_entries'] - prev} small-side entries, probes so far {st['probes']}")
+                prev = st["small_entries"]
         proc, _ = r.counts()
         st = r.stats()
     print(f"{len(s)} edges, {int(proc.sum())} semi-triangles, pool {st['pool_used']} slots used", flush=True)
