@@ -621,6 +621,8 @@ struct SnapHeader {
     uint64_t proc_begin, proc_end;
 };
 constexpr uint64_t kSnapMagic = 0x5245505453544154ull;  // "REPTSTAT"
+// 3: a table bucket holds its 4 ids and then their 4 stream indices (2: ids and indices in two arrays)
+constexpr uint64_t kSnapVersion = 3;
 
 // The arrays of a snapshot after the header, in order: {device pointer, bytes}.
 struct SnapPart {
@@ -674,7 +676,7 @@ int rept_snapshot(rept_state* s, void* h_buf, uint64_t bytes, void* stream) {
     unsigned long long total = sizeof(SnapHeader);
     for (int i = 0; i < np; ++i) total += parts[i].bytes;
     if (bytes < total) return REPT_E_INVAL;
-    SnapHeader h{kSnapMagic, 2, s->cfg.m, s->cfg.c, s->cfg.seed, s->cfg.n_nodes, s->cfg.flags, s->groups,
+    SnapHeader h{kSnapMagic, kSnapVersion, s->cfg.m, s->cfg.c, s->cfg.seed, s->cfg.n_nodes, s->cfg.flags, s->groups,
                  s->next_t, s->h_ctrl->pool_top, s->h_ctrl->self_loops, s->h_ctrl->stored,
                  s->cfg.proc_begin, s->cfg.proc_end};
     std::memcpy(h_buf, &h, sizeof(h));
@@ -692,7 +694,7 @@ int rept_restore(rept_state* s, const void* h_buf, uint64_t bytes, void* stream)
     cudaStream_t st = as_stream(stream);
     SnapHeader h;
     std::memcpy(&h, h_buf, sizeof(h));
-    if (h.magic != kSnapMagic || h.version != 2 || h.m != s->cfg.m || h.c != s->cfg.c || h.seed != s->cfg.seed ||
+    if (h.magic != kSnapMagic || h.version != kSnapVersion || h.m != s->cfg.m || h.c != s->cfg.c || h.seed != s->cfg.seed ||
         h.n_nodes != s->cfg.n_nodes || h.flags != s->cfg.flags || h.groups != s->groups ||
         h.proc_begin != s->cfg.proc_begin || h.proc_end != s->cfg.proc_end)
         return REPT_E_INVAL;

@@ -12,8 +12,12 @@
 //                   compact array cnt_add[n_nodes] first; k_plan moves the
 //                   counts into the records.
 //   pool[]          8-byte slots: per node, an open-addressing (linear probing,
-//                   4-key buckets) table of 2^lg neighbour ids with a parallel
-//                   array of their stream indices (2^lg slots in all), then
+//                   4-key buckets) table of 2^lg neighbour ids and their stream
+//                   indices (2^lg slots in all; for streams with stored colours
+//                   each 32-byte bucket holds its 4 ids and then their 4
+//                   indices, so that an insert or a probe hit touches one
+//                   sector; streams that probe every candidate keep all ids
+//                   first and the indices after them, ids packed densely), then
 //                   the same entries as a packed list of {nbr, eidx} pairs
 //                   (and, for streams with colour words, one word per entry).
 //                   An entry (w, t) of x is the stored edge {x, w} that
@@ -353,6 +357,8 @@ __host__ __device__ __forceinline__ uint32_t id_mask(const StreamDev& d) {
     return d.colours == kColInEntry ? kIdMask : ~0u;
 }
 __host__ __device__ __forceinline__ bool has_words(const StreamDev& d) { return d.colours == kColWords; }
+// The stream's tables are interleaved (key_word) exactly when it stores colours.
+__host__ __device__ __forceinline__ bool tables_interleaved(const StreamDev& d) { return d.colours != kColNone; }
 
 // With one hash group, a wedge (s, w), (l, w) can count only for the processor of colour
 // js = h_0(s, w), and only if that processor exists and h_0(l, w) = js.  The intersection reads js from
@@ -420,6 +426,18 @@ __host__ __device__ __forceinline__ int bin_of_cnt(uint32_t cnt, uint32_t tile_m
 __device__ __forceinline__ uint32_t home_slot(uint32_t w, uint32_t lg) {
     return ((w * 0x9E3779B1u) >> (32u - lg)) & ~3u;
 }
+
+// Word offsets, from the start of a table of 2^lg slots, of slot h's neighbour id and of its stream
+// index.  Interleaved (`inter`): bucket h / 4 occupies words 8 (h / 4) .. 8 (h / 4) + 7, ids first.
+// Split: ids in words 0 .. 2^lg - 1, indices in the next 2^lg words.  key_quad: the 16-byte quad that
+// holds the four ids of the bucket that starts at slot h (h a multiple of 4).
+__host__ __device__ __forceinline__ uint32_t key_word(uint32_t h, bool inter) {
+    return inter ? (((h >> 2) << 3) | (h & 3u)) : h;
+}
+__host__ __device__ __forceinline__ uint32_t eidx_word(uint32_t h, uint32_t lg, bool inter) {
+    return inter ? key_word(h, true) + 4u : (1u << lg) + h;
+}
+__host__ __device__ __forceinline__ uint32_t key_quad(uint32_t h, bool inter) { return inter ? h >> 1 : h >> 2; }
 
 __device__ __forceinline__ unsigned long long pack_slot(uint32_t nbr, uint32_t eidx) {
     return ((unsigned long long)eidx << 32) | nbr;

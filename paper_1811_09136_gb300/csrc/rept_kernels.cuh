@@ -22,16 +22,23 @@ namespace rept {
 // Internal linkage: every translation unit of the library that launches these kernels gets its own copy.
 namespace {
 
-// A node's table of 2^lg slots at pool slot `base` is two arrays of 2^lg uint32: the neighbour ids
-// (keys; probed a 4-key, 16-byte bucket at a time) and then, at the same positions, the stream index
-// of each entry.  Insert (nbr, eidx): claim a key slot with a 32-bit CAS, then store the index.
+// A node's table of 2^lg slots at pool slot `base` holds 2^lg neighbour ids (keys; probed a 4-key,
+// 16-byte bucket at a time) and their stream indices, interleaved per bucket or split (key_word,
+// eidx_word; `inter`).  Insert (nbr, eidx): claim a key slot with a 32-bit CAS, then store the index
+// (in the same sector when interleaved).
 // Returns false only if the table has no empty slot left (impossible while cnt <= capacity / 2).
 // Lookups read whole 4-key buckets, so where a key sits inside its bucket does not matter: an insert
 // tries the slots of a bucket starting from one chosen by other bits of the key, so that keys sharing
 // a home bucket seldom contend for the same slot, and moves to the next bucket only when all four are
 // taken.
+// The slot of its home bucket that an insert of nbr tries first.
+__device__ __forceinline__ uint32_t first_slot(uint32_t nbr, uint32_t lg) {
+    return home_slot(nbr, lg) + ((nbr * 0x85EBCA6Bu) >> 30);
+}
+
+// `tried_first`: the caller's CAS on first_slot(nbr, lg) failed already.
 __device__ __forceinline__ bool table_insert(uint2* pool, unsigned long long base, uint32_t lg, uint32_t nbr,
-                                             uint32_t eidx) {
+                                             uint32_t eidx, bool inter, bool tried_first = false) {
     uint32_t* keys = reinterpret_cast<uint32_t*>(pool + base);
     const uint32_t mask = (1u << lg) - 1u;
     const uint32_t start = (nbr * 0x85EBCA6Bu) >> 30;
@@ -39,9 +46,10 @@ __device__ __forceinline__ bool table_insert(uint2* pool, unsigned long long bas
     for (uint32_t probe = 0; probe <= mask; probe += 4u) {
 #pragma unroll
         for (uint32_t i = 0; i < 4u; ++i) {
+            if (tried_first && probe == 0u && i == 0u) continue;
             const uint32_t h = b + ((start + i) & 3u);
-            if (atomicCAS(keys + h, kEmptyId, nbr) == kEmptyId) {
-                keys[(1u << lg) + h] = eidx;
+            if (atomicCAS(keys + key_word(h, inter), kEmptyId, nbr) == kEmptyId) {
+                keys[eidx_word(h, lg, inter)] = eidx;
                 return true;
             }
         }
@@ -116,8 +124,9 @@ __device__ __forceinline__ uint32_t* list_words(uint2* pool, unsigned long long 
 // Move node x's entries (list of cnt_old entries at old_off) into its new block at new_off: copy the
 // list (and, with `words`, the colour words) and insert each entry's id (`mask` takes it out of the
 // entry) into the new table.  Lanes `rank` of `width` share the work.
-__device__ __forceinline__ bool move_block(uint2* pool, uint32_t mask, bool words, uint32_t old_off, uint32_t cnt_old,
-                                           unsigned long long new_off, uint32_t lg_new, uint32_t rank, uint32_t width) {
+__device__ __forceinline__ bool move_block(uint2* pool, uint32_t mask, bool words, bool inter, uint32_t old_off,
+                                           uint32_t cnt_old, unsigned long long new_off, uint32_t lg_new, uint32_t rank,
+                                           uint32_t width) {
     const uint32_t lg_old = table_lg(cnt_old);
     const unsigned long long old_at = 4ull * old_off + (1ull << lg_old);
     const unsigned long long new_at = 4ull * new_off + (1ull << lg_new);
@@ -128,7 +137,7 @@ __device__ __forceinline__ bool move_block(uint2* pool, uint32_t mask, bool word
         const uint2 e = old_list[j];
         new_list[j] = e;
         if (words) list_words(pool, new_off, lg_new)[j] = list_words(pool, old_off, lg_old)[j];
-        ok &= table_insert(pool, 4ull * new_off, lg_new, e.x & mask, e.y);
+        ok &= table_insert(pool, 4ull * new_off, lg_new, e.x & mask, e.y, inter);
     }
     return ok;
 }
@@ -172,7 +181,7 @@ __device__ __forceinline__ void k_commit_body(const StreamDev& d, const Grid g) 
                     const unsigned long long new_off = top + rel;
                     const bool fits = block_fits(d, 10, m.x, table_lg(m.y)) &&
                                       block_fits(d, 11, new_off, table_lg(cnt_new));
-                    if (fits && !move_block(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, table_lg(cnt_new), 0u,
+                    if (fits && !move_block(d.pool, id_mask(d), has_words(d), tables_interleaved(d), m.x, m.y, new_off, table_lg(cnt_new), 0u,
                                             1u))
                         atomicOr(&d.ctrl->status, kStInternal);
                     d.meta[x] = make_uint4((uint32_t)new_off, cnt_new, m.z, 0u);
@@ -190,7 +199,7 @@ __device__ __forceinline__ void k_commit_body(const StreamDev& d, const Grid g) 
 // the same placement rule as table_insert) and then written out with coalesced stores, by the lanes
 // `rank` of `width` of one warp (BLOCK = false) or of one thread block (BLOCK = true).  The new block
 // is the caller's alone until the batch's inserts run.
-template <bool BLOCK>
+template <bool BLOCK, bool INTER>
 __device__ __forceinline__ bool move_block_smem(uint2* pool, uint32_t id_bits, bool words, uint32_t old_off,
                                                 uint32_t cnt_old, unsigned long long new_off, uint32_t lg_new,
                                                 uint32_t* s_keys, uint32_t* s_eidx, uint32_t rank, uint32_t width) {
@@ -229,10 +238,17 @@ __device__ __forceinline__ bool move_block_smem(uint2* pool, uint32_t id_bits, b
         ok &= placed;
     }
     sync();
-    uint32_t* keys = reinterpret_cast<uint32_t*>(pool + 4ull * new_off);
-    for (uint32_t q = rank; q < cap; q += width) {
-        keys[q] = s_keys[q];
-        keys[cap + q] = s_eidx[q];
+    uint32_t* words_out = reinterpret_cast<uint32_t*>(pool + 4ull * new_off);
+    if (INTER) {  // word q of the table: bucket q / 8, an id (q % 8 < 4) or a stream index
+        for (uint32_t q = rank; q < 2u * cap; q += width) {
+            const uint32_t h = ((q >> 3) << 2) | (q & 3u);
+            words_out[q] = (q & 4u) ? s_eidx[h] : s_keys[h];
+        }
+    } else {
+        for (uint32_t q = rank; q < cap; q += width) {
+            words_out[q] = s_keys[q];
+            words_out[cap + q] = s_eidx[q];
+        }
     }
     return ok;
 }
@@ -257,10 +273,13 @@ __device__ __forceinline__ void k_rehash_big_body(const StreamDev& d, const Grid
         const uint32_t lg_new = table_lg(cnt_new);
         bool ok = true;
         if (fits && (1u << lg_new) <= kMoveSlots && REPT_CHECK(d.ctrl, 14, wid, 8u))
-            ok = move_block_smem<false>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new,
-                                        smem + wid * kMoveSlots, smem + (8u + wid) * kMoveSlots, lane, 32u);
+            ok = tables_interleaved(d)
+                     ? move_block_smem<false, true>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new,
+                                                    smem + wid * kMoveSlots, smem + (8u + wid) * kMoveSlots, lane, 32u)
+                     : move_block_smem<false, false>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new,
+                                                     smem + wid * kMoveSlots, smem + (8u + wid) * kMoveSlots, lane, 32u);
         else if (fits)
-            ok = move_block(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, lane, 32u);
+            ok = move_block(d.pool, id_mask(d), has_words(d), tables_interleaved(d), m.x, m.y, new_off, lg_new, lane, 32u);
         if (!ok) atomicOr(&d.ctrl->status, kStInternal);
         __syncwarp();
         if (lane == 0) d.meta[x] = make_uint4((uint32_t)new_off, cnt_new, m.z, 0u);
@@ -293,10 +312,13 @@ __device__ __forceinline__ void k_rehash_huge_body(const StreamDev& d, const Gri
         const uint32_t lg_new = table_lg(cnt_new);
         bool ok = true;
         if (fits && (1u << lg_new) <= kBlockMoveSlots)  // uniform over the block
-            ok = move_block_smem<true>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, s_keys, s_eidx,
-                                       threadIdx.x, blockDim.x);
+            ok = tables_interleaved(d)
+                     ? move_block_smem<true, true>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, s_keys,
+                                                   s_eidx, threadIdx.x, blockDim.x)
+                     : move_block_smem<true, false>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, s_keys,
+                                                    s_eidx, threadIdx.x, blockDim.x);
         else if (fits)
-            ok = move_block(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, threadIdx.x, blockDim.x);
+            ok = move_block(d.pool, id_mask(d), has_words(d), tables_interleaved(d), m.x, m.y, new_off, lg_new, threadIdx.x, blockDim.x);
         if (!ok) s_bad = 1;
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -356,15 +378,31 @@ __device__ __forceinline__ void k_insert_body(const StreamDev& d, const BatchDev
         uint32_t key = kNoKey;
         WorkItem it{};
         if (valid && u != v) {
+            // list positions: meta[x].z counts this batch's entries of x back down to zero.  The two
+            // counters, the two records and then the first CAS of each table insert are issued
+            // before any result is used, so that their round trips overlap.
+            uint32_t zu = 0u, zv = 0u;
+            if (kept) {
+                zu = atomicSub(&d.meta[u].z, 1u);
+                zv = atomicSub(&d.meta[v].z, 1u);
+            }
             const uint4 mu = d.meta[u], mv = d.meta[v];
             if (kept && block_fits(d, 1, mu.x, table_lg(mu.y)) && block_fits(d, 1, mv.x, table_lg(mv.y))) {
                 const uint32_t t = (uint32_t)(b.t0 + e);
                 const uint32_t lu = table_lg(mu.y), lv = table_lg(mv.y);
-                bool ok = table_insert(d.pool, 4ull * mu.x, lu, v, t);
-                ok &= table_insert(d.pool, 4ull * mv.x, lv, u, t);
+                uint32_t* tu = reinterpret_cast<uint32_t*>(d.pool + 4ull * mu.x);
+                uint32_t* tv = reinterpret_cast<uint32_t*>(d.pool + 4ull * mv.x);
+                const bool inter = tables_interleaved(d);
+                const uint32_t hu = first_slot(v, lu), hv = first_slot(u, lv);
+                const uint32_t cu = atomicCAS(tu + key_word(hu, inter), kEmptyId, v);
+                const uint32_t cv = atomicCAS(tv + key_word(hv, inter), kEmptyId, u);
+                bool ok = true;
+                if (cu == kEmptyId) tu[eidx_word(hu, lu, inter)] = t;
+                else ok = table_insert(d.pool, 4ull * mu.x, lu, v, t, inter, true);
+                if (cv == kEmptyId) tv[eidx_word(hv, lv, inter)] = t;
+                else ok &= table_insert(d.pool, 4ull * mv.x, lv, u, t, inter, true);
                 if (!ok) atomicOr(&ct->status, kStInternal);
-                // list positions: meta[x].z counts this batch's entries of x back down to zero
-                const uint32_t pu = mu.y - atomicSub(&d.meta[u].z, 1u), pv = mv.y - atomicSub(&d.meta[v].z, 1u);
+                const uint32_t pu = mu.y - zu, pv = mv.y - zv;
                 if (REPT_CHECK(ct, 2, pu, list_slots(lu)) && REPT_CHECK(ct, 2, pv, list_slots(lv))) {
                     d.pool[4ull * mu.x + (1ull << lu) + pu] = make_uint2(v | cj, t);
                     d.pool[4ull * mv.x + (1ull << lv) + pv] = make_uint2(u | cj, t);
@@ -493,20 +531,20 @@ __device__ __forceinline__ void k_sort_scatter_body(const StreamDev& d, const Ba
 // home bucket on until w or an empty key shows up.  Returns w's stream index, or kEmptyId when w is
 // absent; `slots` receives the number of keys read.
 __device__ __forceinline__ uint32_t table_find(const uint2* __restrict__ pool, unsigned long long base, uint32_t lg,
-                                               uint32_t w, uint32_t& slots) {
+                                               uint32_t w, uint32_t& slots, bool inter) {
     const uint32_t mask = (1u << lg) - 1u;
     const uint32_t* keys = reinterpret_cast<const uint32_t*>(pool + base);
     const uint4* buckets = reinterpret_cast<const uint4*>(keys);
     uint32_t h = home_slot(w, lg);
-    for (uint32_t probe = 0; probe <= mask; probe += 4u) {
-        const uint4 k4 = buckets[h >> 2];
+    for (uint32_t probe = 0; probe <= mask; probe += 4u) {  // h: the first slot of a bucket
+        const uint4 k4 = buckets[key_quad(h, inter)];
         slots = probe + 4u;
         int at = -1;
         if (k4.x == w) at = 0;
         else if (k4.y == w) at = 1;
         else if (k4.z == w) at = 2;
         else if (k4.w == w) at = 3;
-        if (at >= 0) return keys[(1u << lg) + h + (uint32_t)at];
+        if (at >= 0) return keys[eidx_word(h + (uint32_t)at, lg, inter)];
         if (k4.x == kEmptyId || k4.y == kEmptyId || k4.z == kEmptyId || k4.w == kEmptyId) return kEmptyId;
         h = (h + 4u) & mask;
     }
@@ -527,7 +565,7 @@ __global__ void k_check_dups(StreamDev d, BatchDev b, unsigned long long mask) {
         if (u == v || u >= d.n_nodes || v >= d.n_nodes) continue;
         const uint4 mu = d.meta[u];
         uint32_t ns;
-        if (mu.y != 0u && table_find(d.pool, 4ull * mu.x, table_lg(mu.y), v, ns) != kEmptyId) dup = true;
+        if (mu.y != 0u && table_find(d.pool, 4ull * mu.x, table_lg(mu.y), v, ns, tables_interleaved(d)) != kEmptyId) dup = true;
         const unsigned long long key = ((unsigned long long)(u < v ? u : v) << 32) | (u < v ? v : u);
         unsigned long long h = splitmix64(key) & mask;
         for (unsigned long long probe = 0; probe <= mask; ++probe) {
@@ -557,6 +595,7 @@ __device__ __forceinline__ void pair_event(const StreamDev& d, uint32_t t, uint3
 // DIFF: decide each group's colour agreement from the two hash values' difference (same_colour: one
 // remainder only when they agree), which pays where wedges are counted under several groups (the
 // probe variant); the single-group variants form both colours, which keeps their registers lower.
+// DIFF is set exactly for the probe variant, whose streams keep split tables (tables_interleaved).
 template <bool DIFF>
 __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, uint32_t l, uint32_t w,
                                                 unsigned long long* s_proc) {
@@ -586,8 +625,8 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
                 if (t_sw == kEmptyId) {  // the wedge's two stream indices, looked up once
                     uint32_t ns;
                     const uint4 ms = d.meta[s], ml = d.meta[l];
-                    t_sw = table_find(d.pool, 4ull * ms.x, table_lg(ms.y), w, ns);
-                    t_lw = table_find(d.pool, 4ull * ml.x, table_lg(ml.y), w, ns);
+                    t_sw = table_find(d.pool, 4ull * ms.x, table_lg(ms.y), w, ns, !DIFF);
+                    t_lw = table_find(d.pool, 4ull * ml.x, table_lg(ml.y), w, ns, !DIFF);
                 }
                 pair_event(d, t_sw, k);
                 pair_event(d, t_lw, k);
@@ -668,7 +707,8 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
             pass = words_may_count(d, x.l, ws, list_words(d.pool, x.off_s, x.lgs & 0xFFu)[j]);
         if (pass) {
             uint32_t nslots = 0;
-            const uint32_t tl = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, ws, nslots);
+            // the single-stream kernels' streams: split tables exactly in the probe variant (DIFF)
+            const uint32_t tl = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, ws, nslots, !DIFF);
             if (WORK) { ++wk.probes; wk.pslots += nslots; }
             has = tl < x.t;  // kEmptyId (absent) is never < t
             w = ws;
@@ -728,7 +768,9 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
     const uint32_t mask = id_mask(d);
     const uint32_t* keys_l = reinterpret_cast<const uint32_t*>(d.pool + base_l);
     const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
-    const uint32_t cap_l = 1u << lg_l;
+    // the probe variant's streams keep split tables; the other kernels' streams may be of either kind
+    // only on the group path
+    const bool inter = MODE == (int)kColNone ? false : tables_interleaved(d);
     const unsigned below = (1u << lane) - 1u;
     // PREFETCH: the next pass's entries are loaded while the current pass is tested
     uint4 nq[2];
@@ -788,7 +830,7 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
                 w[p] = v ? queue[k0 + 32u * p + lane] : kEmptyId;
                 h[p] = home_slot(w[p], lg_l);
                 bk[p] = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-                if (v) bk[p] = __ldg(&buckets_l[h[p] >> 2]);
+                if (v) bk[p] = __ldg(&buckets_l[key_quad(h[p], inter)]);
             }
 #pragma unroll
             for (int p = 0; p < kProbesPerLane; ++p) {
@@ -798,9 +840,9 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
                 if (w[p] != kEmptyId) {
                     uint32_t ns = 4u;
                     if (at >= 0) {
-                        r[p] = __ldg(&keys_l[cap_l + h[p] + (uint32_t)at]);
+                        r[p] = __ldg(&keys_l[eidx_word(h[p] + (uint32_t)at, lg_l, inter)]);
                     } else if (b.x != kEmptyId && b.y != kEmptyId && b.z != kEmptyId && b.w != kEmptyId) {
-                        r[p] = table_find(d.pool, base_l, lg_l, w[p], ns);  // rare: the bucket is full
+                        r[p] = table_find(d.pool, base_l, lg_l, w[p], ns, inter);  // rare: the bucket is full
                     }
                     if (WORK) { ++wk.probes; wk.pslots += ns; }
                 }
@@ -816,6 +858,157 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
             for (uint32_t r = lane; r < rest; r += 32u) queue[r] = queue[k0 + r];
             n_q = rest;
             __syncwarp();
+        }
+    }
+}
+
+// Coloured streams (kColInEntry), warp classes: scan first, probe later.  A warp reads an item's
+// smaller-endpoint list 128 entries per pass (two 16-byte loads per lane, two entries each) and tests
+// every entry's colour against the larger endpoint by hash alone.  The few entries that pass (about
+// 1/m) join the warp's candidate queue together with the index of their work item; the queue is
+// probed 64 candidates at a time, whatever items they come from, so that an item with a handful of
+// candidates does not pay for a probe round of its own.
+struct CandQueue {
+    uint32_t* w;     // [kQueue] candidate neighbour w
+    uint32_t* item;  // [kQueue] its work item, an index into srec
+    uint32_t n;      // warp-uniform
+};
+
+// Probe candidates k0 .. k0 + take - 1 (take <= 64), two per lane: both items' records and then both
+// home buckets are loaded before either is examined.  A hit older than its edge is a closed wedge.
+template <bool WORK>
+__device__ __forceinline__ void cand_probe(const StreamDev& d, const CandQueue& cq, uint32_t k0, uint32_t take,
+                                           unsigned long long* s_proc, MatchQueue& mq, Work& wk) {
+    const unsigned lane = threadIdx.x & 31u;
+    uint32_t w[2], h[2], lg[2], tt[2], ss[2], ll[2];
+    unsigned long long base[2];
+    uint4 bk[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const uint32_t k = 32u * p + lane;
+        bool v = k < take;
+        w[p] = kEmptyId;
+        lg[p] = 2u;
+        base[p] = 0ull;
+        tt[p] = ss[p] = ll[p] = 0u;
+        bk[p] = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
+        if (v) {
+            const uint4* rec = reinterpret_cast<const uint4*>(d.srec + cq.item[k0 + k]);
+            const uint4 r0 = rec[0], r1 = rec[1];  // {s, l, off_s, off_l}, {t, lgs, cnt_s, key}
+            w[p] = cq.w[k0 + k];
+            ss[p] = r0.x;
+            ll[p] = r0.y;
+            base[p] = 4ull * r0.w;
+            tt[p] = r1.x;
+            lg[p] = r1.y >> 8;
+            if (!block_fits(d, 7, r0.w, lg[p])) {
+                v = false;
+                w[p] = kEmptyId;
+            }
+        }
+        h[p] = home_slot(w[p], lg[p]);
+        if (v) bk[p] = __ldg(reinterpret_cast<const uint4*>(d.pool + base[p]) + key_quad(h[p], true));
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const uint4 b = bk[p];
+        const int at = b.x == w[p] ? 0 : b.y == w[p] ? 1 : b.z == w[p] ? 2 : b.w == w[p] ? 3 : -1;
+        uint32_t r = kEmptyId;
+        if (w[p] != kEmptyId) {
+            uint32_t ns = 4u;
+            if (at >= 0)
+                r = __ldg(reinterpret_cast<const uint32_t*>(d.pool + base[p]) + eidx_word(h[p] + (uint32_t)at, lg[p], true));
+            else if (b.x != kEmptyId && b.y != kEmptyId && b.z != kEmptyId && b.w != kEmptyId)
+                r = table_find(d.pool, base[p], lg[p], w[p], ns, true);  // rare: the bucket is full
+            if (WORK) { ++wk.probes; wk.pslots += ns; }
+        }
+        mq_push<WORK, false>(d, mq, w[p] != kEmptyId && r < tt[p], ss[p], ll[p], w[p], s_proc, wk);
+    }
+}
+
+// Probe the queue's full rounds of 64 (`all`: everything) and move the rest to the front.
+template <bool WORK>
+__device__ __forceinline__ void cand_flush(const StreamDev& d, CandQueue& cq, bool all, unsigned long long* s_proc,
+                                           MatchQueue& mq, Work& wk) {
+    __syncwarp();
+    uint32_t k0 = 0;
+    for (; all ? k0 < cq.n : k0 + 64u <= cq.n; k0 += 64u)
+        cand_probe<WORK>(d, cq, k0, cq.n - k0 < 64u ? cq.n - k0 : 64u, s_proc, mq, wk);
+    if (all) {
+        cq.n = 0;
+    } else if (k0) {  // the rest (< 64 <= k0 candidates): source and destination ranges are disjoint
+        const uint32_t rest = cq.n - k0;
+        const unsigned lane = threadIdx.x & 31u;
+        for (uint32_t r = lane; r < rest; r += 32u) {
+            cq.w[r] = cq.w[k0 + r];
+            cq.item[r] = cq.item[k0 + r];
+        }
+        cq.n = rest;
+    }
+    __syncwarp();
+}
+
+template <bool WORK>
+__device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int cls, uint32_t grab,
+                                                        unsigned long long* s_proc, CandQueue& cq, MatchQueue& mq,
+                                                        Work& wk) {
+    static_assert(63 + 128 <= kQueue, "candidate queue too small");
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned below = (1u << lane) - 1u;
+    const unsigned long long count = d.ctrl->bin_count[cls];
+    const uint32_t first = (uint32_t)d.ctrl->bin_start[cls];
+    const WorkItem* items = d.srec + first;
+    for (;;) {
+        unsigned long long i0 = 0;
+        if (lane == 0) i0 = atomicAdd(&d.ctrl->bin_next[cls], (unsigned long long)grab);
+        i0 = __shfl_sync(0xFFFFFFFFu, i0, 0);
+        if (i0 >= count) break;
+        const unsigned long long i1 = i0 + grab < count ? i0 + grab : count;
+        for (unsigned long long i = i0; i < i1; ++i) {
+            const WorkItem x = items[i];
+            const uint32_t n_s = x.cnt_s, l = x.l, t = x.t, lgs = x.lgs & 0xFFu;
+            if (WORK && lane == 0) { wk.entries += n_s; wk.slots += n_s; }
+            if (!(block_fits(d, 5, x.off_s, lgs) && REPT_CHECK(d.ctrl, 6, n_s, list_slots(lgs) + 1u) &&
+                  block_fits(d, 7, x.off_l, x.lgs >> 8)))
+                continue;  // (uniform over the warp: x is)
+            // the list (32-byte aligned), two entries per 16-byte load; a lane past the end re-reads
+            // the last pair, and its entries are masked off by position
+            const uint4* list = reinterpret_cast<const uint4*>(d.pool + 4ull * x.off_s + (1ull << lgs));
+            const uint32_t last_pair = (n_s - 1u) >> 1;
+            const uint32_t item = first + (uint32_t)i;
+            for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
+                uint4 q[2];
+#pragma unroll
+                for (uint32_t half = 0; half < 2; ++half) {
+                    const uint32_t pr = (j0 >> 1) + 32u * half + lane;
+                    q[half] = list[pr < last_pair ? pr : last_pair];
+                }
+#pragma unroll
+                for (uint32_t half = 0; half < 2; ++half) {
+                    if (j0 + 64u * half >= n_s) break;  // an empty half: uniform skip
+                    const uint32_t jj = j0 + 64u * half + 2u * lane;
+                    const uint32_t w1 = q[half].x & kIdMask, w2 = q[half].z & kIdMask;
+                    const bool a1 = (jj < n_s) & (q[half].y < t) & wedge_may_count(d, l, w1, q[half].x >> kIdBits);
+                    const bool a2 =
+                        (jj + 1u < n_s) & (q[half].w < t) & wedge_may_count(d, l, w2, q[half].z >> kIdBits);
+                    const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
+                    if (m1 | m2) {  // rare (about 1/m of the entries pass): uniform
+                        if (a1) {
+                            const uint32_t k = cq.n + __popc(m1 & below);
+                            cq.w[k] = w1;
+                            cq.item[k] = item;
+                        }
+                        cq.n += __popc(m1);
+                        if (a2) {
+                            const uint32_t k = cq.n + __popc(m2 & below);
+                            cq.w[k] = w2;
+                            cq.item[k] = item;
+                        }
+                        cq.n += __popc(m2);
+                    }
+                }
+                if (cq.n >= 64u) cand_flush<WORK>(d, cq, false, s_proc, mq, wk);
+            }
         }
     }
 }
@@ -872,7 +1065,9 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint
 template <bool WORK, int MODE>
 __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const BatchDev& b) {
     extern __shared__ unsigned long long s_proc[];
+    constexpr bool CAND = MODE == (int)kColInEntry;  // the scan-first warp path (candidate queue)
     __shared__ uint32_t s_queue[256 / 32][kQueue];
+    __shared__ uint32_t s_item[CAND ? 256 / 32 : 1][kQueue];
     __shared__ uint32_t s_match[256 / 32][3][kMatchQ];
     for (uint32_t i = threadIdx.x; i < d.c; i += blockDim.x) s_proc[i] = 0ull;
     __syncthreads();
@@ -880,6 +1075,7 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
     const unsigned wid = threadIdx.x >> 5;
     uint32_t* queue = s_queue[wid];
     MatchQueue mq{s_match[wid][0], s_match[wid][1], s_match[wid][2], 0u};
+    CandQueue cq{queue, s_item[CAND ? wid : 0], 0u};
     Work wk;
     if (d.ctrl->status == 0u) {
         // WORK: per class, the probes issued and the warp-cycles spent (clock64 around each drain)
@@ -899,10 +1095,18 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
                 p0 = p1;
             }
         };
-        drain_warp_bin<WORK, MODE>(d, 5, kGrabHub, s_proc, queue, mq, wk);
-        mark(5);
-        drain_warp_bin<WORK, MODE>(d, 4, kGrabMid, s_proc, queue, mq, wk);
-        mark(4);
+        if (CAND) {
+            drain_warp_bin_coloured<WORK>(d, 5, kGrabHub, s_proc, cq, mq, wk);
+            mark(5);
+            drain_warp_bin_coloured<WORK>(d, 4, kGrabMid, s_proc, cq, mq, wk);
+            if (cq.n) cand_flush<WORK>(d, cq, true, s_proc, mq, wk);
+            mark(4);
+        } else {
+            drain_warp_bin<WORK, MODE>(d, 5, kGrabHub, s_proc, queue, mq, wk);
+            mark(5);
+            drain_warp_bin<WORK, MODE>(d, 4, kGrabMid, s_proc, queue, mq, wk);
+            mark(4);
+        }
         drain_tile_bin<32, WORK, MODE == (int)kColNone>(d, 3, s_proc, mq, wk);
         mark(3);
         drain_tile_bin<16, WORK, MODE == (int)kColNone>(d, 2, s_proc, mq, wk);
@@ -1101,7 +1305,7 @@ __device__ __forceinline__ void group_drain_tiles(const StreamDev* __restrict__ 
                     const uint32_t ws = es.x & id_mask(d);
                     if (es.y < x.t && (d.colours != kColInEntry || wedge_may_count(d, x.l, ws, es.x >> kIdBits))) {
                         uint32_t nslots = 0;
-                        has = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, ws, nslots) < x.t;
+                        has = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, ws, nslots, tables_interleaved(d)) < x.t;
                         w = ws;
                     }
                 }
@@ -1285,12 +1489,13 @@ __global__ void __launch_bounds__(256) k_rehash_big_multi(const StreamDev* __res
     k_rehash_big_body(sd, launch_grid(), smem);
 }
 
-__global__ void __launch_bounds__(1024) k_rehash_huge(StreamDev d) {
+// Two blocks of 1024 threads per SM (32 registers a thread), so that the whole grid is resident.
+__global__ void __launch_bounds__(1024, 2) k_rehash_huge(StreamDev d) {
     __shared__ uint32_t smem[kMoveSmemWords];
     k_rehash_huge_body(d, launch_grid(), smem);
 }
 
-__global__ void __launch_bounds__(1024) k_rehash_huge_multi(const StreamDev* __restrict__ ds,
+__global__ void __launch_bounds__(1024, 2) k_rehash_huge_multi(const StreamDev* __restrict__ ds,
                                                               const BatchDev* __restrict__ bs) {
     (void)bs;
     __shared__ StreamDev sd;
@@ -1472,19 +1677,6 @@ __global__ void __launch_bounds__(256, REPT_WORDS_BLOCKS) k_intersect_words(Stre
 template <bool WORK>
 __global__ void __launch_bounds__(256, 8) k_intersect_probe(StreamDev d, BatchDev b) {
     k_intersect_body<WORK, (int)kColNone>(d, b);
-}
-
-template <bool WORK>
-__global__ void __launch_bounds__(256, 5) k_intersect_multi(const StreamDev* __restrict__ ds,
-                                                             const BatchDev* __restrict__ bs) {
-    __shared__ StreamDev sd;
-    __shared__ BatchDev sb;
-    if (threadIdx.x == 0) {
-        sd = ds[blockIdx.y];
-        sb = bs[blockIdx.y];
-    }
-    __syncthreads();
-    k_intersect_body<WORK, (int)kColInEntry>(sd, sb);
 }
 
 // tau_hat_v = f * sum_i tau_v^(i), f formed in double on the host.
