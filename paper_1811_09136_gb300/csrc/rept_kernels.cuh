@@ -16,6 +16,8 @@
 // edge t is exactly the sequential algorithm's state before t.
 #pragma once
 
+#include <type_traits>
+
 #include "rept_common.cuh"
 
 namespace rept {
@@ -740,14 +742,14 @@ constexpr int kProbesPerLane = REPT_PROBES_PER_LANE;  // probes each lane keeps 
 #define REPT_WORDS_BLOCKS 6
 #endif
 
-// MODE: the colour storage this instantiation tests (kColInEntry: hash-bound, the next pass is
-// prefetched; kColWords: one hash per hash group and entry; kColNone: probe-bound, fewer registers,
-// more warps per SM).  A stream whose colours differ from MODE is served as kColNone.
+// MODE: the colour storage of the stream (kColWords: one hash per hash group and entry; kColNone:
+// probe-bound, fewer registers, more warps per SM).  Streams with colours in their entries take the
+// scan-first path (drain_warp_bin_coloured) instead.
 // `push(has, w)` (warp-collective) takes each probed key w and whether it closed a wedge.
 template <bool WORK, int MODE, class Push>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, uint32_t* queue, Work& wk,
                                                Push&& push) {
-    constexpr bool PREFETCH = MODE == (int)kColInEntry;
+    static_assert(MODE != (int)kColInEntry, "coloured entries take the scan-first path");
     constexpr uint32_t kRound = 32u * kProbesPerLane;
     static_assert(kRound - 1 + 128 <= kQueue, "key queue too small");
     const unsigned lane = threadIdx.x & 31u;
@@ -758,21 +760,17 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
           block_fits(d, 7, x.off_l, lg_l)))
         return;  // (uniform over the warp: x is)
     // the smaller endpoint's entry list (32-byte aligned), read 128 entries per pass, two per 16-byte
-    // load; with colours, each entry's id and colour share its first word
+    // load
     const unsigned long long at_s = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu));
     const uint4* list = reinterpret_cast<const uint4*>(d.pool + at_s);
-    const bool cols = MODE == (int)kColInEntry && d.colours == kColInEntry;
-    const bool wcols = MODE == (int)kColWords && d.colours == kColWords;
+    const bool wcols = MODE == (int)kColWords;
     // kColWords: the colour words of the entries, two per 8-byte load
     const uint2* words = reinterpret_cast<const uint2*>(list_words(d.pool, x.off_s, x.lgs & 0xFFu));
     const uint32_t mask = id_mask(d);
     const uint32_t* keys_l = reinterpret_cast<const uint32_t*>(d.pool + base_l);
     const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
-    // the probe variant's streams keep split tables; the other kernels' streams may be of either kind
-    // only on the group path
-    const bool inter = MODE == (int)kColNone ? false : tables_interleaved(d);
+    const bool inter = MODE != (int)kColNone;  // the probe variant's streams keep split tables
     const unsigned below = (1u << lane) - 1u;
-    // PREFETCH: the next pass's entries are loaded while the current pass is tested
     uint4 nq[2];
     uint2 nw[2];
     auto load_pass = [&](uint32_t j0) {
@@ -787,15 +785,13 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
             }
         }
     };
-    if (PREFETCH) load_pass(0u);
     uint32_t n_q = 0;
 
     for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
         if (!REPT_CHECK(d.ctrl, 8, n_q, kRound)) break;
-        if (!PREFETCH) load_pass(j0);
+        load_pass(j0);
         const uint4 cq[2] = {nq[0], nq[1]};
         const uint2 cw[2] = {nw[0], nw[1]};
-        if (PREFETCH && j0 + 128u < n_s) load_pass(j0 + 128u);
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
             if (j0 + 64u * half >= n_s) break;  // an empty half (short lists, last passes): uniform skip
@@ -803,10 +799,7 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
             const uint4 q = cq[half];
             const uint32_t w1 = q.x & mask, w2 = q.z & mask;
             bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
-            if (cols) {
-                a1 = a1 & wedge_may_count(d, x.l, w1, q.x >> kIdBits);
-                a2 = a2 & wedge_may_count(d, x.l, w2, q.z >> kIdBits);
-            } else if (wcols) {
+            if (wcols) {
                 a1 = a1 && words_may_count(d, x.l, w1, cw[half].x);
                 a2 = a2 && words_may_count(d, x.l, w2, cw[half].y);
             }
@@ -868,9 +861,19 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
 // 1/m) join the warp's candidate queue together with the index of their work item; the queue is
 // probed 64 candidates at a time, whatever items they come from, so that an item with a handful of
 // candidates does not pay for a probe round of its own.
+#ifndef REPT_SCAN_LOADS
+#define REPT_SCAN_LOADS 4
+#endif
+#ifndef REPT_SCAN_FULL
+#define REPT_SCAN_FULL 1
+#endif
+constexpr uint32_t kScanLoads = REPT_SCAN_LOADS;  // 16-byte loads per lane and pass
+constexpr uint32_t kScanPass = 64u * kScanLoads;  // entries per pass
+constexpr bool kScanFull = REPT_SCAN_FULL != 0;  // passes inside the list skip the position checks
+constexpr uint32_t kCandQ = 64u + kScanPass;       // candidate queue slots per warp
 struct CandQueue {
-    uint32_t* w;     // [kQueue] candidate neighbour w
-    uint32_t* item;  // [kQueue] its work item, an index into srec
+    uint32_t* w;     // [kCandQ] candidate neighbour w
+    uint32_t* item;  // [kCandQ] its work item, an index into srec
     uint32_t n;      // warp-uniform
 };
 
@@ -952,7 +955,7 @@ template <bool WORK>
 __device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int cls, uint32_t grab,
                                                         unsigned long long* s_proc, CandQueue& cq, MatchQueue& mq,
                                                         Work& wk) {
-    static_assert(63 + 128 <= kQueue, "candidate queue too small");
+    static_assert(63 + kScanPass <= kCandQ, "candidate queue too small");  // flushed at 64 after a pass
     const unsigned lane = threadIdx.x & 31u;
     const unsigned below = (1u << lane) - 1u;
     const unsigned long long count = d.ctrl->bin_count[cls];
@@ -976,21 +979,24 @@ __device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int 
             const uint4* list = reinterpret_cast<const uint4*>(d.pool + 4ull * x.off_s + (1ull << lgs));
             const uint32_t last_pair = (n_s - 1u) >> 1;
             const uint32_t item = first + (uint32_t)i;
-            for (uint32_t j0 = 0; j0 < n_s; j0 += 128u) {
-                uint4 q[2];
+            // one pass: kScanLoads 16-byte loads per lane (2 kScanLoads entries), all issued first;
+            // FULL: the pass lies inside the list, so no entry needs its position checked
+            auto pass = [&](uint32_t j0, auto full) {
+                constexpr bool FULL = decltype(full)::value;
+                uint4 q[kScanLoads];
 #pragma unroll
-                for (uint32_t half = 0; half < 2; ++half) {
-                    const uint32_t pr = (j0 >> 1) + 32u * half + lane;
-                    q[half] = list[pr < last_pair ? pr : last_pair];
+                for (uint32_t h = 0; h < kScanLoads; ++h) {
+                    const uint32_t pr = (j0 >> 1) + 32u * h + lane;
+                    q[h] = list[FULL || pr < last_pair ? pr : last_pair];
                 }
 #pragma unroll
-                for (uint32_t half = 0; half < 2; ++half) {
-                    if (j0 + 64u * half >= n_s) break;  // an empty half: uniform skip
-                    const uint32_t jj = j0 + 64u * half + 2u * lane;
-                    const uint32_t w1 = q[half].x & kIdMask, w2 = q[half].z & kIdMask;
-                    const bool a1 = (jj < n_s) & (q[half].y < t) & wedge_may_count(d, l, w1, q[half].x >> kIdBits);
+                for (uint32_t h = 0; h < kScanLoads; ++h) {
+                    if (!FULL && j0 + 64u * h >= n_s) break;  // an empty part: uniform skip
+                    const uint32_t jj = j0 + 64u * h + 2u * lane;
+                    const uint32_t w1 = q[h].x & kIdMask, w2 = q[h].z & kIdMask;
+                    const bool a1 = (FULL || jj < n_s) & (q[h].y < t) & wedge_may_count(d, l, w1, q[h].x >> kIdBits);
                     const bool a2 =
-                        (jj + 1u < n_s) & (q[half].w < t) & wedge_may_count(d, l, w2, q[half].z >> kIdBits);
+                        (FULL || jj + 1u < n_s) & (q[h].w < t) & wedge_may_count(d, l, w2, q[h].z >> kIdBits);
                     const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
                     if (m1 | m2) {  // rare (about 1/m of the entries pass): uniform
                         if (a1) {
@@ -1008,7 +1014,11 @@ __device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int 
                     }
                 }
                 if (cq.n >= 64u) cand_flush<WORK>(d, cq, false, s_proc, mq, wk);
-            }
+            };
+            uint32_t j0 = 0;
+            if (kScanFull)
+                for (; j0 + kScanPass <= n_s; j0 += kScanPass) pass(j0, std::true_type{});
+            for (; j0 < n_s; j0 += kScanPass) pass(j0, std::false_type{});
         }
     }
 }
@@ -1066,16 +1076,16 @@ template <bool WORK, int MODE>
 __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const BatchDev& b) {
     extern __shared__ unsigned long long s_proc[];
     constexpr bool CAND = MODE == (int)kColInEntry;  // the scan-first warp path (candidate queue)
-    __shared__ uint32_t s_queue[256 / 32][kQueue];
-    __shared__ uint32_t s_item[CAND ? 256 / 32 : 1][kQueue];
+    __shared__ uint32_t s_queue[CAND ? 1 : 256 / 32][kQueue];  // intersect_warp's key queue
+    __shared__ uint32_t s_cand[CAND ? 256 / 32 : 1][2][kCandQ];
     __shared__ uint32_t s_match[256 / 32][3][kMatchQ];
     for (uint32_t i = threadIdx.x; i < d.c; i += blockDim.x) s_proc[i] = 0ull;
     __syncthreads();
     const unsigned lane = threadIdx.x & 31u;
     const unsigned wid = threadIdx.x >> 5;
-    uint32_t* queue = s_queue[wid];
+    uint32_t* queue = s_queue[CAND ? 0 : wid];
     MatchQueue mq{s_match[wid][0], s_match[wid][1], s_match[wid][2], 0u};
-    CandQueue cq{queue, s_item[CAND ? wid : 0], 0u};
+    CandQueue cq{s_cand[CAND ? wid : 0][0], s_cand[CAND ? wid : 0][1], 0u};
     Work wk;
     if (d.ctrl->status == 0u) {
         // WORK: per class, the probes issued and the warp-cycles spent (clock64 around each drain)
@@ -1095,7 +1105,7 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
                 p0 = p1;
             }
         };
-        if (CAND) {
+        if constexpr (CAND) {
             drain_warp_bin_coloured<WORK>(d, 5, kGrabHub, s_proc, cq, mq, wk);
             mark(5);
             drain_warp_bin_coloured<WORK>(d, 4, kGrabMid, s_proc, cq, mq, wk);
@@ -1315,14 +1325,100 @@ __device__ __forceinline__ void group_drain_tiles(const StreamDev* __restrict__ 
     }
 }
 
-__device__ __forceinline__ void group_drain_warps(const StreamDev* __restrict__ ds, uint32_t k, int cls, uint32_t grab,
-                                                  const unsigned long long* __restrict__ pref,
-                                                  unsigned long long* __restrict__ cursor, uint32_t* queue,
-                                                  GroupQueue& q) {
+// Warp classes of a group: the scan-first scheme of drain_warp_bin_coloured over all streams of the
+// group, a candidate also naming its stream.  A stream without colours in its entries passes every
+// entry older than the edge to the probes.
+struct GroupCand {
+    uint32_t* w;     // [kCandQ] candidate neighbour w
+    uint32_t* item;  // [kCandQ] its work item, an index into its stream's srec
+    uint32_t* sid;   // [kCandQ] its stream
+    uint32_t n;      // warp-uniform
+};
+
+__device__ __forceinline__ void gcand_probe(const StreamDev* __restrict__ ds, const GroupCand& cq, uint32_t k0,
+                                            uint32_t take, GroupQueue& q) {
     const unsigned lane = threadIdx.x & 31u;
+    uint32_t w[2], h[2], lg[2], tt[2], ss[2], ll[2], sd[2];
+    const uint2* pool[2];
+    bool inter[2];
+    unsigned long long base[2];
+    uint4 bk[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const uint32_t k = 32u * p + lane;
+        bool v = k < take;
+        w[p] = kEmptyId;
+        lg[p] = 2u;
+        base[p] = 0ull;
+        tt[p] = ss[p] = ll[p] = sd[p] = 0u;
+        pool[p] = nullptr;
+        inter[p] = true;
+        bk[p] = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
+        if (v) {
+            sd[p] = cq.sid[k0 + k];
+            const StreamDev& d = ds[sd[p]];
+            const uint4* rec = reinterpret_cast<const uint4*>(d.srec + cq.item[k0 + k]);
+            const uint4 r0 = rec[0], r1 = rec[1];  // {s, l, off_s, off_l}, {t, lgs, cnt_s, key}
+            w[p] = cq.w[k0 + k];
+            ss[p] = r0.x;
+            ll[p] = r0.y;
+            base[p] = 4ull * r0.w;
+            tt[p] = r1.x;
+            lg[p] = r1.y >> 8;
+            pool[p] = d.pool;
+            inter[p] = tables_interleaved(d);
+            if (!block_fits(d, 7, r0.w, lg[p])) {
+                v = false;
+                w[p] = kEmptyId;
+            }
+        }
+        h[p] = home_slot(w[p], lg[p]);
+        if (v) bk[p] = __ldg(reinterpret_cast<const uint4*>(pool[p] + base[p]) + key_quad(h[p], inter[p]));
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const uint4 b = bk[p];
+        const int at = b.x == w[p] ? 0 : b.y == w[p] ? 1 : b.z == w[p] ? 2 : b.w == w[p] ? 3 : -1;
+        uint32_t r = kEmptyId;
+        if (w[p] != kEmptyId) {
+            uint32_t ns = 4u;
+            if (at >= 0)
+                r = __ldg(reinterpret_cast<const uint32_t*>(pool[p] + base[p]) +
+                          eidx_word(h[p] + (uint32_t)at, lg[p], inter[p]));
+            else if (b.x != kEmptyId && b.y != kEmptyId && b.z != kEmptyId && b.w != kEmptyId)
+                r = table_find(pool[p], base[p], lg[p], w[p], ns, inter[p]);  // rare: the bucket is full
+        }
+        gq_push(ds, q, w[p] != kEmptyId && r < tt[p], sd[p], ss[p], ll[p], w[p]);
+    }
+}
+
+__device__ __forceinline__ void gcand_flush(const StreamDev* __restrict__ ds, GroupCand& cq, bool all, GroupQueue& q) {
+    __syncwarp();
+    uint32_t k0 = 0;
+    for (; all ? k0 < cq.n : k0 + 64u <= cq.n; k0 += 64u) gcand_probe(ds, cq, k0, cq.n - k0 < 64u ? cq.n - k0 : 64u, q);
+    if (all) {
+        cq.n = 0;
+    } else if (k0) {  // the rest (< 64 <= k0 candidates): source and destination ranges are disjoint
+        const uint32_t rest = cq.n - k0;
+        const unsigned lane = threadIdx.x & 31u;
+        for (uint32_t r = lane; r < rest; r += 32u) {
+            cq.w[r] = cq.w[k0 + r];
+            cq.item[r] = cq.item[k0 + r];
+            cq.sid[r] = cq.sid[k0 + r];
+        }
+        cq.n = rest;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void group_drain_warps_cand(const StreamDev* __restrict__ ds, uint32_t k, int cls,
+                                                       uint32_t grab, const unsigned long long* __restrict__ pref,
+                                                       unsigned long long* __restrict__ cursor, GroupCand& cq,
+                                                       GroupQueue& q) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned below = (1u << lane) - 1u;
     const unsigned long long* pc = pref + cls * (k + 1);
     const unsigned long long total = pc[k];
-    Work wk;  // not tallied on this path
     for (;;) {
         unsigned long long i0 = 0;
         if (lane == 0) i0 = atomicAdd(&cursor[cls], (unsigned long long)grab);
@@ -1333,27 +1429,76 @@ __device__ __forceinline__ void group_drain_warps(const StreamDev* __restrict__ 
         for (unsigned long long i = i0; i < i1; ++i) {
             sid = group_stream_of(pc, k, i, sid);
             const StreamDev& d = ds[sid];
-            const WorkItem x = group_item(d, cls, i - pc[sid]);
-            intersect_warp<false, (int)kColInEntry>(d, x, queue, wk, [&](bool has, uint32_t w) {
-                gq_push(ds, q, has, sid, x.s, x.l, w);
-            });
+            const uint32_t item = (uint32_t)(d.ctrl->bin_start[cls] + (i - pc[sid]));
+            const WorkItem x = d.srec[item];
+            const uint32_t n_s = x.cnt_s, l = x.l, t = x.t, lgs = x.lgs & 0xFFu;
+            if (!(block_fits(d, 5, x.off_s, lgs) && REPT_CHECK(d.ctrl, 6, n_s, list_slots(lgs) + 1u) &&
+                  block_fits(d, 7, x.off_l, x.lgs >> 8)))
+                continue;  // (uniform over the warp: x is)
+            const uint4* list = reinterpret_cast<const uint4*>(d.pool + 4ull * x.off_s + (1ull << lgs));
+            const uint32_t last_pair = (n_s - 1u) >> 1;
+            const uint32_t mask = id_mask(d);
+            const bool open = d.colours != kColInEntry;  // no colour test: every older entry is probed
+            auto pass = [&](uint32_t j0, auto full) {
+                constexpr bool FULL = decltype(full)::value;
+                uint4 qv[kScanLoads];
+#pragma unroll
+                for (uint32_t hh = 0; hh < kScanLoads; ++hh) {
+                    const uint32_t pr = (j0 >> 1) + 32u * hh + lane;
+                    qv[hh] = list[FULL || pr < last_pair ? pr : last_pair];
+                }
+#pragma unroll
+                for (uint32_t hh = 0; hh < kScanLoads; ++hh) {
+                    if (!FULL && j0 + 64u * hh >= n_s) break;  // an empty part: uniform skip
+                    const uint32_t jj = j0 + 64u * hh + 2u * lane;
+                    const uint32_t w1 = qv[hh].x & mask, w2 = qv[hh].z & mask;
+                    const bool a1 = (FULL || jj < n_s) & (qv[hh].y < t) &
+                                    (open | wedge_may_count(d, l, w1, qv[hh].x >> kIdBits));
+                    const bool a2 = (FULL || jj + 1u < n_s) & (qv[hh].w < t) &
+                                    (open | wedge_may_count(d, l, w2, qv[hh].z >> kIdBits));
+                    const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
+                    if (m1 | m2) {
+                        if (a1) {
+                            const uint32_t kk = cq.n + __popc(m1 & below);
+                            cq.w[kk] = w1;
+                            cq.item[kk] = item;
+                            cq.sid[kk] = sid;
+                        }
+                        cq.n += __popc(m1);
+                        if (a2) {
+                            const uint32_t kk = cq.n + __popc(m2 & below);
+                            cq.w[kk] = w2;
+                            cq.item[kk] = item;
+                            cq.sid[kk] = sid;
+                        }
+                        cq.n += __popc(m2);
+                    }
+                }
+                if (cq.n >= 64u) gcand_flush(ds, cq, false, q);
+            };
+            uint32_t j0 = 0;
+            if (kScanFull)
+                for (; j0 + kScanPass <= n_s; j0 += kScanPass) pass(j0, std::true_type{});
+            for (; j0 < n_s; j0 += kScanPass) pass(j0, std::false_type{});
         }
     }
 }
 
-// Shared memory of the group intersection, per block of 8 warps: a key queue and a match queue of
-// four arrays (stream, s, l, w) per warp.
-constexpr uint32_t kGroupSmemWords = 8u * kQueue + 8u * 4u * kMatchQ;
+// Shared memory of the group intersection, per block of 8 warps: a candidate queue of three arrays
+// (w, item, stream) and a match queue of four arrays (stream, s, l, w) per warp.
+constexpr uint32_t kGroupSmemWords = 8u * 3u * kCandQ + 8u * 4u * kMatchQ;
 
 __device__ __forceinline__ void intersect_group_body(const StreamDev* __restrict__ ds, uint32_t k,
                                                      const unsigned long long* __restrict__ pref,
                                                      unsigned long long* __restrict__ cursor, uint32_t* smem) {
     const unsigned wid = threadIdx.x >> 5;
-    uint32_t* queue = smem + wid * kQueue;
-    uint32_t* mq = smem + 8u * kQueue + wid * 4u * kMatchQ;
+    uint32_t* cw = smem + wid * 3u * kCandQ;
+    uint32_t* mq = smem + 8u * 3u * kCandQ + wid * 4u * kMatchQ;
     GroupQueue q{mq, mq + kMatchQ, mq + 2u * kMatchQ, mq + 3u * kMatchQ, 0u};
-    group_drain_warps(ds, k, 5, kGrabHub, pref, cursor, queue, q);
-    group_drain_warps(ds, k, 4, kGrabMid, pref, cursor, queue, q);
+    GroupCand cq{cw, cw + kCandQ, cw + 2u * kCandQ, 0u};
+    group_drain_warps_cand(ds, k, 5, kGrabHub, pref, cursor, cq, q);
+    group_drain_warps_cand(ds, k, 4, kGrabMid, pref, cursor, cq, q);
+    if (cq.n) gcand_flush(ds, cq, true, q);
     group_drain_tiles<32>(ds, k, 3, pref, cursor, q);
     group_drain_tiles<16>(ds, k, 2, pref, cursor, q);
     group_drain_tiles<8>(ds, k, 1, pref, cursor, q);
