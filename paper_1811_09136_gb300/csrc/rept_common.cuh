@@ -375,6 +375,21 @@ __device__ __forceinline__ bool wedge_may_count(const StreamDev& d, uint32_t l, 
     return (js - d.pbeg < d.pcount) & mod_equals_nobranch(z, js, d.fm);
 }
 
+// The scans' form of wedge_may_count: a superset test.  It never rejects an entry whose wedge can
+// count, and may pass a few whose wedge cannot; count_wedge decides every queued wedge exactly.
+// z mod m = js implies that m divides z - js, i.e. that r = rotr((z - js) q^-1, k) <= floor((2^64 - 1)
+// / m); only the high words are compared (a pass rate of about 1/m + 2^-32).  The range test of
+// wedge_may_count is left out: every entry of a list carries a kept colour (its edge is stored
+// because this state's processor of that colour keeps it), and z < js, which the exact test
+// excludes, has probability below 2^-56.
+__device__ __forceinline__ bool colour_may_match(const StreamDev& d, uint32_t l, uint32_t w, uint32_t js) {
+    const uint64_t lo = l < w ? l : w, hi = l < w ? w : l;
+    const uint64_t z = splitmix64(((lo << 32) | hi) ^ d.seed);
+    const uint64_t y = (z - js) * d.fm.qinv;
+    const uint32_t r_hi = __funnelshift_r((uint32_t)(y >> 32), (uint32_t)y, d.fm.k);
+    return r_hi <= (uint32_t)(d.fm.lim >> 32);
+}
+
 // With several hash groups (kColWords), a wedge (s, w), (l, w) can count only for a group k whose
 // colour js_k = h_k(s, w) names a kept processor and equals h_k(l, w).  The word cw holds every js_k
 // (read from s's entry); the groups are tried in order and the first that agrees decides, so an

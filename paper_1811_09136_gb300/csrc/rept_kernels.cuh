@@ -994,9 +994,9 @@ __device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int 
                     if (!FULL && j0 + 64u * h >= n_s) break;  // an empty part: uniform skip
                     const uint32_t jj = j0 + 64u * h + 2u * lane;
                     const uint32_t w1 = q[h].x & kIdMask, w2 = q[h].z & kIdMask;
-                    const bool a1 = (FULL || jj < n_s) & (q[h].y < t) & wedge_may_count(d, l, w1, q[h].x >> kIdBits);
+                    const bool a1 = (FULL || jj < n_s) & (q[h].y < t) & colour_may_match(d, l, w1, q[h].x >> kIdBits);
                     const bool a2 =
-                        (FULL || jj + 1u < n_s) & (q[h].w < t) & wedge_may_count(d, l, w2, q[h].z >> kIdBits);
+                        (FULL || jj + 1u < n_s) & (q[h].w < t) & colour_may_match(d, l, w2, q[h].z >> kIdBits);
                     const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
                     if (m1 | m2) {  // rare (about 1/m of the entries pass): uniform
                         if (a1) {
@@ -1453,9 +1453,9 @@ __device__ __forceinline__ void group_drain_warps_cand(const StreamDev* __restri
                     const uint32_t jj = j0 + 64u * hh + 2u * lane;
                     const uint32_t w1 = qv[hh].x & mask, w2 = qv[hh].z & mask;
                     const bool a1 = (FULL || jj < n_s) & (qv[hh].y < t) &
-                                    (open | wedge_may_count(d, l, w1, qv[hh].x >> kIdBits));
+                                    (open | colour_may_match(d, l, w1, qv[hh].x >> kIdBits));
                     const bool a2 = (FULL || jj + 1u < n_s) & (qv[hh].w < t) &
-                                    (open | wedge_may_count(d, l, w2, qv[hh].z >> kIdBits));
+                                    (open | colour_may_match(d, l, w2, qv[hh].z >> kIdBits));
                     const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
                     if (m1 | m2) {
                         if (a1) {
