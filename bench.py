@@ -181,14 +181,14 @@ def peaks():
 # thread operations) per cycle; scaled by the SM clock sampled during the timed region.
 SMS, SMSP_PER_SM, LANES = 152, 4, 32
 # Thread operations the intersection needs per unit of work (the algorithmic count, not what the
-# compiler emits): per scanned list entry with a stored colour, the colour test of the larger
-# endpoint's edge -- the ordered key (min, max, shift/or: 3), the seed xor (2), SplitMix64 (64-bit
-# add 2, three 64-bit xor-shifts 3 x 4, two 64-bit multiplies by constants 2 x 3: 20), the
-# divisibility test (64-bit compare, subtract, multiply, rotate, compare: 2 + 2 + 3 + 2 + 2 = 11) --
-# plus the entry's own age test and id mask (2): 38; per scanned entry without stored colours, the
+# compiler emits): per scanned list entry with a stored colour, the colour filter of the larger
+# endpoint's edge -- the ordered key (min, max: 2), the seed xor (2), SplitMix64 (64-bit add 2, three
+# 64-bit xor-shifts 3 x 4, two 64-bit multiplies by constants 2 x 3: 20), the high word of the
+# divisibility test (64-bit subtract 2, multiply 3, funnel shift 1, compare 1: 7) -- plus the entry's
+# id mask, colour extraction and age test (3): 34; per scanned entry without stored colours, the
 # age test and mask (2); per probe, the home-bucket hash and the 4-key compare (8); per counted
 # wedge, the colours of both edges (2 x 31) and the three local updates (3): 65.
-OPS_ENTRY_COLOURED, OPS_ENTRY_PLAIN, OPS_PROBE, OPS_WEDGE = 38, 2, 8, 65
+OPS_ENTRY_COLOURED, OPS_ENTRY_PLAIN, OPS_PROBE, OPS_WEDGE = 34, 2, 8, 65
 
 
 # --------------------------------------------------------------------------- oracle digests
