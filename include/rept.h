@@ -149,14 +149,18 @@ typedef struct rept_state rept_state;
  */
 int rept_create(const rept_config* cfg, void* stream, rept_state** out);
 
-/* rept_reset: return the handle to the empty stream, keeping its allocations; clears a sticky error. */
+/*
+ * rept_reset: return the handle to the empty stream, keeping its allocations;
+ * clears a sticky error.  The clearing is enqueued on `stream` (the call does
+ * not wait); the adjacency pool is reused as it is, each table getting its
+ * empty keys when its block is handed out again.
+ */
 int rept_reset(rept_state* s, void* stream);
 
 /*
- * rept_reset_async: as rept_reset, without waiting, and the next stream uses
- * hash seed `seed` (s_0): the whole adjacency pool is cleared (not only its
- * used part) and everything is enqueued on `stream`.  For servers that reuse
- * a handle for the next stream of the same shape.
+ * rept_reset_async: as rept_reset, and the next stream uses hash seed `seed`
+ * (s_0).  For servers that reuse a handle for the next stream of the same
+ * shape.
  */
 int rept_reset_async(rept_state* s, uint64_t seed, void* stream);
 

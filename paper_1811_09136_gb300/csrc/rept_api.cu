@@ -435,17 +435,13 @@ int rept_create(const rept_config* cfg, void* stream, rept_state** out) {
     return REPT_OK;
 }
 
+// The pool itself is not cleared: blocks are handed out again from its start, and each new table
+// gets its empty keys when its block is handed out (init_table_keys and the shared-memory builds).
 int rept_reset(rept_state* s, void* stream) {
     if (!s) return REPT_E_INVAL;
     cudaStream_t st = as_stream(stream);
     StreamDev& d = s->d;
     const size_t n = d.n_nodes;
-    // tables handed out so far go back to all-ones (empty)
-    REPT_CUDA(cudaMemcpyAsync(s->h_ctrl, d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-    REPT_CUDA(cudaStreamSynchronize(st));
-    unsigned long long used = s->h_ctrl->pool_top;
-    if (used > d.pool_quads) used = d.pool_quads;
-    if (used) REPT_CUDA(cudaMemsetAsync(d.pool, 0xFF, used * 32ull, st));
     REPT_CUDA(cudaMemsetAsync(d.meta, 0, n * sizeof(uint4), st));
     REPT_CUDA(cudaMemsetAsync(d.cnt_add, 0, n * sizeof(uint32_t), st));
     REPT_CUDA(cudaMemsetAsync(d.local, 0, n * sizeof(unsigned long long), st));
@@ -459,7 +455,6 @@ int rept_reset(rept_state* s, void* stream) {
     }
     if (d.local_proc) REPT_CUDA(cudaMemsetAsync(d.local_proc, 0, (size_t)d.c * n * sizeof(unsigned long long), st));
     REPT_CUDA(cudaMemsetAsync(d.ctrl, 0, sizeof(Ctrl), st));
-    REPT_CUDA(cudaStreamSynchronize(st));
     memset(s->h_ctrl, 0, sizeof(Ctrl));
     s->next_t = 0;
     return REPT_OK;
@@ -472,7 +467,6 @@ int rept_reset_async(rept_state* s, uint64_t seed, void* stream) {
     s->cfg.seed = seed;
     d.seed = seed;
     const size_t n = d.n_nodes;
-    REPT_CUDA(cudaMemsetAsync(d.pool, 0xFF, d.pool_quads * 32ull, st));
     REPT_CUDA(cudaMemsetAsync(d.meta, 0, n * sizeof(uint4), st));
     REPT_CUDA(cudaMemsetAsync(d.cnt_add, 0, n * sizeof(uint32_t), st));
     REPT_CUDA(cudaMemsetAsync(d.local, 0, n * sizeof(unsigned long long), st));

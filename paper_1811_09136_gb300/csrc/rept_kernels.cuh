@@ -144,14 +144,27 @@ __device__ __forceinline__ bool move_block(uint2* pool, uint32_t mask, bool word
     return ok;
 }
 
+// Set every key of the new table of 2^lg slots at `off_quads` to empty (lanes `rank` of `width`).  The
+// pool is not cleared between streams: a block's table gets its empty keys when the block is handed
+// out, from here or from the shared-memory builds, which write the whole table.  (Stream indices are
+// read only beside a matching key, so they need no initial value.)
+__device__ __forceinline__ void init_table_keys(uint2* pool, unsigned long long off_quads, uint32_t lg, bool inter,
+                                                uint32_t rank, uint32_t width) {
+    uint4* quads = reinterpret_cast<uint4*>(pool + 4ull * off_quads);
+    const uint4 empty = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
+    for (uint32_t b = rank; b < (1u << lg) / 4u; b += width) quads[inter ? 2u * b : b] = empty;
+}
+
 // New tables of at most kMoveSlots slots are rebuilt in shared memory by a warp (k_rehash_big), those
 // of at most kBlockMoveSlots by a thread block (k_rehash_huge); larger ones are built in place.
+constexpr uint32_t kInlineSlots = 32;  // k_commit's own moves (one thread each)
 constexpr uint32_t kMoveSlots = 512;
 constexpr uint32_t kBlockMoveSlots = 4096;
 
 // Publish the new entry counts of the touched nodes and move the blocks that were re-allocated.
-// One thread per touched node; a block holding more than 8 entries is left to k_rehash_big (a warp
-// each, new tables of at most kMoveSlots slots) or k_rehash_huge (a thread block each).  meta[x].z
+// One thread per touched node moves a block of at most 8 entries into a new table of at most
+// kInlineSlots slots; other blocks are left to k_rehash_big (a warp each, new tables of at most
+// kMoveSlots slots) or k_rehash_huge (a thread block each).  meta[x].z
 // keeps the batch's new-entry count for k_insert, which counts it back down to zero; a batch that is not
 // applied clears it here.
 __device__ __forceinline__ void k_commit_body(const StreamDev& d, const Grid g) {
@@ -176,15 +189,16 @@ __device__ __forceinline__ void k_commit_body(const StreamDev& d, const Grid g) 
                 const uint32_t rel = d.grow_rel[i];
                 if (rel == kNoGrow) {
                     d.meta[x].y = cnt_new;
-                } else if (m.y > 8u) {
+                } else if (m.y > 8u || (1u << table_lg(cnt_new)) > kInlineSlots) {
                     defer = (1u << table_lg(cnt_new)) <= kMoveSlots;
                     huge = !defer;
                 } else {
                     const unsigned long long new_off = top + rel;
                     const bool fits = block_fits(d, 10, m.x, table_lg(m.y)) &&
                                       block_fits(d, 11, new_off, table_lg(cnt_new));
-                    if (fits && !move_block(d.pool, id_mask(d), has_words(d), tables_interleaved(d), m.x, m.y, new_off, table_lg(cnt_new), 0u,
-                                            1u))
+                    if (fits) init_table_keys(d.pool, new_off, table_lg(cnt_new), tables_interleaved(d), 0u, 1u);
+                    if (fits && !move_block(d.pool, id_mask(d), has_words(d), tables_interleaved(d), m.x, m.y, new_off,
+                                            table_lg(cnt_new), 0u, 1u))
                         atomicOr(&d.ctrl->status, kStInternal);
                     d.meta[x] = make_uint4((uint32_t)new_off, cnt_new, m.z, 0u);
                 }
@@ -280,8 +294,11 @@ __device__ __forceinline__ void k_rehash_big_body(const StreamDev& d, const Grid
                                                     smem + wid * kMoveSlots, smem + (8u + wid) * kMoveSlots, lane, 32u)
                      : move_block_smem<false, false>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new,
                                                      smem + wid * kMoveSlots, smem + (8u + wid) * kMoveSlots, lane, 32u);
-        else if (fits)
+        else if (fits) {
+            init_table_keys(d.pool, new_off, lg_new, tables_interleaved(d), lane, 32u);
+            __syncwarp();
             ok = move_block(d.pool, id_mask(d), has_words(d), tables_interleaved(d), m.x, m.y, new_off, lg_new, lane, 32u);
+        }
         if (!ok) atomicOr(&d.ctrl->status, kStInternal);
         __syncwarp();
         if (lane == 0) d.meta[x] = make_uint4((uint32_t)new_off, cnt_new, m.z, 0u);
@@ -319,8 +336,12 @@ __device__ __forceinline__ void k_rehash_huge_body(const StreamDev& d, const Gri
                                                    s_eidx, threadIdx.x, blockDim.x)
                      : move_block_smem<true, false>(d.pool, id_mask(d), has_words(d), m.x, m.y, new_off, lg_new, s_keys,
                                                     s_eidx, threadIdx.x, blockDim.x);
-        else if (fits)
-            ok = move_block(d.pool, id_mask(d), has_words(d), tables_interleaved(d), m.x, m.y, new_off, lg_new, threadIdx.x, blockDim.x);
+        else if (fits) {  // (uniform over the block) built in place: empty keys first
+            init_table_keys(d.pool, new_off, lg_new, tables_interleaved(d), threadIdx.x, blockDim.x);
+            __syncthreads();
+            ok = move_block(d.pool, id_mask(d), has_words(d), tables_interleaved(d), m.x, m.y, new_off, lg_new,
+                            threadIdx.x, blockDim.x);
+        }
         if (!ok) s_bad = 1;
         __syncthreads();
         if (threadIdx.x == 0) {
