@@ -972,10 +972,13 @@ __device__ __forceinline__ void cand_flush(const StreamDev& d, CandQueue& cq, bo
     __syncwarp();
 }
 
+// `t0`: the batch's first stream index.  A list holds the entries of earlier batches first (appends
+// and block moves keep list order), so a pass whose last entry is older than t0 holds only entries
+// older than every edge of the batch, and its entries skip the age test.
 template <bool WORK>
 __device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int cls, uint32_t grab,
                                                         unsigned long long* s_proc, CandQueue& cq, MatchQueue& mq,
-                                                        Work& wk) {
+                                                        Work& wk, uint32_t t0) {
     static_assert(63 + kScanPass <= kCandQ, "candidate queue too small");  // flushed at 64 after a pass
     const unsigned lane = threadIdx.x & 31u;
     const unsigned below = (1u << lane) - 1u;
@@ -1002,22 +1005,19 @@ __device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int 
             const uint32_t item = first + (uint32_t)i;
             // one pass: kScanLoads 16-byte loads per lane (2 kScanLoads entries), all issued first;
             // FULL: the pass lies inside the list, so no entry needs its position checked
-            auto pass = [&](uint32_t j0, auto full) {
-                constexpr bool FULL = decltype(full)::value;
-                uint4 q[kScanLoads];
-#pragma unroll
-                for (uint32_t h = 0; h < kScanLoads; ++h) {
-                    const uint32_t pr = (j0 >> 1) + 32u * h + lane;
-                    q[h] = list[FULL || pr < last_pair ? pr : last_pair];
-                }
+            // the tests of one pass on loaded entries q; FULL: inside the list (no position test);
+            // OLD: every entry older than the batch (no age test)
+            auto test = [&](const uint4 (&q)[kScanLoads], uint32_t j0, auto full, auto old) {
+                constexpr bool FULL = decltype(full)::value, OLD = decltype(old)::value;
 #pragma unroll
                 for (uint32_t h = 0; h < kScanLoads; ++h) {
                     if (!FULL && j0 + 64u * h >= n_s) break;  // an empty part: uniform skip
                     const uint32_t jj = j0 + 64u * h + 2u * lane;
                     const uint32_t w1 = q[h].x & kIdMask, w2 = q[h].z & kIdMask;
-                    const bool a1 = (FULL || jj < n_s) & (q[h].y < t) & colour_may_match(d, l, w1, q[h].x >> kIdBits);
+                    const bool a1 =
+                        (FULL || jj < n_s) & (OLD || q[h].y < t) & colour_may_match(d, l, w1, q[h].x >> kIdBits);
                     const bool a2 =
-                        (FULL || jj + 1u < n_s) & (q[h].w < t) & colour_may_match(d, l, w2, q[h].z >> kIdBits);
+                        (FULL || jj + 1u < n_s) & (OLD || q[h].w < t) & colour_may_match(d, l, w2, q[h].z >> kIdBits);
                     const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
                     if (m1 | m2) {  // rare (about 1/m of the entries pass): uniform
                         if (a1) {
@@ -1035,6 +1035,19 @@ __device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int 
                     }
                 }
                 if (cq.n >= 64u) cand_flush<WORK>(d, cq, false, s_proc, mq, wk);
+            };
+            auto pass = [&](uint32_t j0, auto full) {
+                constexpr bool FULL = decltype(full)::value;
+                uint4 q[kScanLoads];
+#pragma unroll
+                for (uint32_t h = 0; h < kScanLoads; ++h) {
+                    const uint32_t pr = (j0 >> 1) + 32u * h + lane;
+                    q[h] = list[FULL || pr < last_pair ? pr : last_pair];
+                }
+                if (FULL && __shfl_sync(0xFFFFFFFFu, q[kScanLoads - 1].w, 31) < t0)
+                    test(q, j0, full, std::true_type{});
+                else
+                    test(q, j0, full, std::false_type{});
             };
             uint32_t j0 = 0;
             if (kScanFull)
@@ -1127,9 +1140,9 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
             }
         };
         if constexpr (CAND) {
-            drain_warp_bin_coloured<WORK>(d, 5, kGrabHub, s_proc, cq, mq, wk);
+            drain_warp_bin_coloured<WORK>(d, 5, kGrabHub, s_proc, cq, mq, wk, (uint32_t)b.t0);
             mark(5);
-            drain_warp_bin_coloured<WORK>(d, 4, kGrabMid, s_proc, cq, mq, wk);
+            drain_warp_bin_coloured<WORK>(d, 4, kGrabMid, s_proc, cq, mq, wk, (uint32_t)b.t0);
             if (cq.n) cand_flush<WORK>(d, cq, true, s_proc, mq, wk);
             mark(4);
         } else {
