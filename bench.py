@@ -370,7 +370,7 @@ def single_leg(name, m, c, seed, steps, warmup, dev, pg, digests, clock_mhz_hint
         "work": {k: st[k] for k in ("small_entries", "probes", "wedges", "counted", "stored_edges",
                                     "class_items", "class_probes", "class_cycles")},
         "l2": (f"inputs and state larger than L2, no flush: {ws_bytes / 1e9:.2f} GB touched per step (edges, "
-               f"node blocks in use, per-node arrays; every step also resets them)"
+               f"node blocks written as they are handed out, per-node arrays cleared at every step's start)"
                if ws_bytes > (129 << 20) else "working set fits in L2 (no flush)"),
         "k3": {"bytes": k3_bytes, "ops": k3_ops, "seconds": k3_s, "launches": k3_n // max(steps, 1),
                "coloured": coloured},
