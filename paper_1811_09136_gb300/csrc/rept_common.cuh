@@ -406,6 +406,24 @@ __device__ __forceinline__ bool words_may_count(const StreamDev& d, uint32_t l, 
     return false;
 }
 
+// The scans' superset form of words_may_count (as colour_may_match is of wedge_may_count): every
+// group of this state is tested, each with the high words of its divisibility test, and the results
+// are combined with | (no early exit, so the lanes of a warp stay together).  Groups whose colour
+// js_k no processor keeps may pass too; count_wedge decides every queued wedge exactly.
+__device__ __forceinline__ bool words_may_match(const StreamDev& d, uint32_t l, uint32_t w, uint32_t cw) {
+    const uint64_t lo = l < w ? l : w, hi = l < w ? w : l;
+    const uint64_t key = (lo << 32) | hi;
+    const uint32_t lim_hi = (uint32_t)(d.fm.lim >> 32);
+    uint64_t sk = group_seed(d.seed, d.kbeg);
+    bool any = false;
+    for (uint32_t k = d.kbeg; k < d.kend; ++k, sk += kGoldenGamma) {
+        const uint32_t js = (cw >> (k * d.cbits)) & d.cmask;
+        const uint64_t y = (splitmix64(key ^ sk) - js) * d.fm.qinv;
+        any |= __funnelshift_r((uint32_t)(y >> 32), (uint32_t)y, d.fm.k) <= lim_hi;
+    }
+    return any;
+}
+
 // log2 of the table capacity for cnt entries: capacity = max(4, nextpow2(2*cnt)); 0 when empty.
 __host__ __device__ __forceinline__ uint32_t table_lg(uint32_t cnt) {
     if (cnt == 0) return 0;

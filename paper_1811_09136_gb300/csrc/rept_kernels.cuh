@@ -615,13 +615,15 @@ __device__ __forceinline__ void pair_event(const StreamDev& d, uint32_t t, uint3
     if (atomicAdd(&d.pair_evt[idx], 1u) == 0u) d.pair_list[atomicAdd(&d.ctrl->n_pairs, 1ull)] = (uint32_t)idx;
 }
 
-// DIFF: decide each group's colour agreement from the two hash values' difference (same_colour: one
-// remainder only when they agree), which pays where wedges are counted under several groups (the
-// probe variant); the single-group variants form both colours, which keeps their registers lower.
-// DIFF is set exactly for the probe variant, whose streams keep split tables (tables_interleaved).
-template <bool DIFF>
+// MODE: the stream's colour storage (the kernel variant).  DIFF: decide each group's colour agreement
+// from the two hash values' difference (same_colour: one remainder only when they agree), which pays
+// where wedges are counted under several groups (streams without colours in their entries); streams
+// with colours in their entries form both colours, which keeps their registers lower.  INTER: the
+// stream's tables are interleaved (tables_interleaved), i.e. it stores colours.
+template <int MODE>
 __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, uint32_t l, uint32_t w,
                                                 unsigned long long* s_proc) {
+    constexpr bool DIFF = MODE != (int)kColInEntry, INTER = MODE != (int)kColNone;
     if (!REPT_CHECK(d.ctrl, 9, max(w, max(s, l)), d.n_nodes)) return 0u;
     uint32_t found = 0, found2 = 0;
     uint32_t t_sw = kEmptyId, t_lw = kEmptyId;
@@ -648,8 +650,8 @@ __device__ __forceinline__ uint32_t count_wedge(const StreamDev& d, uint32_t s, 
                 if (t_sw == kEmptyId) {  // the wedge's two stream indices, looked up once
                     uint32_t ns;
                     const uint4 ms = d.meta[s], ml = d.meta[l];
-                    t_sw = table_find(d.pool, 4ull * ms.x, table_lg(ms.y), w, ns, !DIFF);
-                    t_lw = table_find(d.pool, 4ull * ml.x, table_lg(ml.y), w, ns, !DIFF);
+                    t_sw = table_find(d.pool, 4ull * ms.x, table_lg(ms.y), w, ns, INTER);
+                    t_lw = table_find(d.pool, 4ull * ml.x, table_lg(ml.y), w, ns, INTER);
                 }
                 pair_event(d, t_sw, k);
                 pair_event(d, t_lw, k);
@@ -679,20 +681,20 @@ struct MatchQueue {
     uint32_t n;
 };
 
-template <bool WORK, bool DIFF>
+template <bool WORK, int MODE>
 __device__ __forceinline__ void mq_flush(const StreamDev& d, MatchQueue& q, uint32_t take,
                                          unsigned long long* s_proc, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
     if (lane < take) {
         const uint32_t i = q.n - take + lane;
-        const uint32_t f = count_wedge<DIFF>(d, q.s[i], q.l[i], q.w[i], s_proc);
+        const uint32_t f = count_wedge<MODE>(d, q.s[i], q.l[i], q.w[i], s_proc);
         if (WORK) wk.counted += f;
     }
     q.n -= take;
     __syncwarp();
 }
 
-template <bool WORK, bool DIFF>
+template <bool WORK, int MODE>
 __device__ __forceinline__ void mq_push(const StreamDev& d, MatchQueue& q, bool has, uint32_t s, uint32_t l,
                                         uint32_t w, unsigned long long* s_proc, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
@@ -707,12 +709,12 @@ __device__ __forceinline__ void mq_push(const StreamDev& d, MatchQueue& q, bool 
     }
     q.n += __popc(mask);
     __syncwarp();
-    if (q.n >= 32u) mq_flush<WORK, DIFF>(d, q, 32u, s_proc, wk);
+    if (q.n >= 32u) mq_flush<WORK, MODE>(d, q, 32u, s_proc, wk);
 }
 
 // Edges whose smaller endpoint has at most TILE entries: one tile of TILE lanes per edge, one list
 // entry per lane.
-template <int TILE, bool WORK, bool DIFF>
+template <int TILE, bool WORK, int MODE>
 __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkItem& x, bool valid,
                                                unsigned long long* s_proc, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u, j = lane & (TILE - 1);
@@ -730,14 +732,14 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
             pass = words_may_count(d, x.l, ws, list_words(d.pool, x.off_s, x.lgs & 0xFFu)[j]);
         if (pass) {
             uint32_t nslots = 0;
-            // the single-stream kernels' streams: split tables exactly in the probe variant (DIFF)
-            const uint32_t tl = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, ws, nslots, !DIFF);
+            // the single-stream kernels' streams: split tables exactly in the probe variant
+            const uint32_t tl = table_find(d.pool, 4ull * x.off_l, x.lgs >> 8, ws, nslots, MODE != (int)kColNone);
             if (WORK) { ++wk.probes; wk.pslots += nslots; }
             has = tl < x.t;  // kEmptyId (absent) is never < t
             w = ws;
         }
     }
-    mq_push<WORK, DIFF>(d, mq, has, x.s, x.l, w, s_proc, wk);
+    mq_push<WORK, MODE>(d, mq, has, x.s, x.l, w, s_proc, wk);
 }
 
 // Edges whose smaller endpoint has more entries: a warp per edge.  Each pass reads 128 entries of
@@ -763,14 +765,14 @@ constexpr int kProbesPerLane = REPT_PROBES_PER_LANE;  // probes each lane keeps 
 #define REPT_WORDS_BLOCKS 6
 #endif
 
-// MODE: the colour storage of the stream (kColWords: one hash per hash group and entry; kColNone:
-// probe-bound, fewer registers, more warps per SM).  Streams with colours in their entries take the
-// scan-first path (drain_warp_bin_coloured) instead.
+// Streams without stored colours (MODE kColNone): every entry older than the edge is probed, so the
+// path is probe-bound and runs with fewer registers and more warps per SM.  Streams that store
+// colours take the scan-first path (drain_warp_bin_coloured) instead.
 // `push(has, w)` (warp-collective) takes each probed key w and whether it closed a wedge.
 template <bool WORK, int MODE, class Push>
 __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkItem& x, uint32_t* queue, Work& wk,
                                                Push&& push) {
-    static_assert(MODE != (int)kColInEntry, "coloured entries take the scan-first path");
+    static_assert(MODE == (int)kColNone, "streams that store colours take the scan-first path");
     constexpr uint32_t kRound = 32u * kProbesPerLane;
     static_assert(kRound - 1 + 128 <= kQueue, "key queue too small");
     const unsigned lane = threadIdx.x & 31u;
@@ -784,26 +786,18 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
     // load
     const unsigned long long at_s = 4ull * x.off_s + (1ull << (x.lgs & 0xFFu));
     const uint4* list = reinterpret_cast<const uint4*>(d.pool + at_s);
-    const bool wcols = MODE == (int)kColWords;
-    // kColWords: the colour words of the entries, two per 8-byte load
-    const uint2* words = reinterpret_cast<const uint2*>(list_words(d.pool, x.off_s, x.lgs & 0xFFu));
     const uint32_t mask = id_mask(d);
     const uint32_t* keys_l = reinterpret_cast<const uint32_t*>(d.pool + base_l);
     const uint4* buckets_l = reinterpret_cast<const uint4*>(keys_l);
-    const bool inter = MODE != (int)kColNone;  // the probe variant's streams keep split tables
+    const bool inter = false;  // these streams keep split tables
     const unsigned below = (1u << lane) - 1u;
     uint4 nq[2];
-    uint2 nw[2];
     auto load_pass = [&](uint32_t j0) {
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
             const uint32_t jj = j0 + 64u * half + 2u * lane;
             nq[half] = make_uint4(kEmptyId, kEmptyId, kEmptyId, kEmptyId);
-            nw[half] = make_uint2(0u, 0u);
-            if (jj < n_s) {
-                nq[half] = list[jj >> 1];
-                if (wcols) nw[half] = words[jj >> 1];
-            }
+            if (jj < n_s) nq[half] = list[jj >> 1];
         }
     };
     uint32_t n_q = 0;
@@ -812,18 +806,13 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
         if (!REPT_CHECK(d.ctrl, 8, n_q, kRound)) break;
         load_pass(j0);
         const uint4 cq[2] = {nq[0], nq[1]};
-        const uint2 cw[2] = {nw[0], nw[1]};
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
             if (j0 + 64u * half >= n_s) break;  // an empty half (short lists, last passes): uniform skip
             const uint32_t jj = j0 + 64u * half + 2u * lane;
             const uint4 q = cq[half];
             const uint32_t w1 = q.x & mask, w2 = q.z & mask;
-            bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
-            if (wcols) {
-                a1 = a1 && words_may_count(d, x.l, w1, cw[half].x);
-                a2 = a2 && words_may_count(d, x.l, w2, cw[half].y);
-            }
+            const bool a1 = jj < n_s && q.y < x.t, a2 = jj + 1u < n_s && q.w < x.t;
             const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
             if (a1) queue[n_q + __popc(m1 & below)] = w1;
             n_q += __popc(m1);
@@ -900,7 +889,7 @@ struct CandQueue {
 
 // Probe candidates k0 .. k0 + take - 1 (take <= 64), two per lane: both items' records and then both
 // home buckets are loaded before either is examined.  A hit older than its edge is a closed wedge.
-template <bool WORK>
+template <bool WORK, int MODE>
 __device__ __forceinline__ void cand_probe(const StreamDev& d, const CandQueue& cq, uint32_t k0, uint32_t take,
                                            unsigned long long* s_proc, MatchQueue& mq, Work& wk) {
     const unsigned lane = threadIdx.x & 31u;
@@ -946,18 +935,18 @@ __device__ __forceinline__ void cand_probe(const StreamDev& d, const CandQueue& 
                 r = table_find(d.pool, base[p], lg[p], w[p], ns, true);  // rare: the bucket is full
             if (WORK) { ++wk.probes; wk.pslots += ns; }
         }
-        mq_push<WORK, false>(d, mq, w[p] != kEmptyId && r < tt[p], ss[p], ll[p], w[p], s_proc, wk);
+        mq_push<WORK, MODE>(d, mq, w[p] != kEmptyId && r < tt[p], ss[p], ll[p], w[p], s_proc, wk);
     }
 }
 
 // Probe the queue's full rounds of 64 (`all`: everything) and move the rest to the front.
-template <bool WORK>
+template <bool WORK, int MODE>
 __device__ __forceinline__ void cand_flush(const StreamDev& d, CandQueue& cq, bool all, unsigned long long* s_proc,
                                            MatchQueue& mq, Work& wk) {
     __syncwarp();
     uint32_t k0 = 0;
     for (; all ? k0 < cq.n : k0 + 64u <= cq.n; k0 += 64u)
-        cand_probe<WORK>(d, cq, k0, cq.n - k0 < 64u ? cq.n - k0 : 64u, s_proc, mq, wk);
+        cand_probe<WORK, MODE>(d, cq, k0, cq.n - k0 < 64u ? cq.n - k0 : 64u, s_proc, mq, wk);
     if (all) {
         cq.n = 0;
     } else if (k0) {  // the rest (< 64 <= k0 candidates): source and destination ranges are disjoint
@@ -975,7 +964,7 @@ __device__ __forceinline__ void cand_flush(const StreamDev& d, CandQueue& cq, bo
 // `t0`: the batch's first stream index.  A list holds the entries of earlier batches first (appends
 // and block moves keep list order), so a pass whose last entry is older than t0 holds only entries
 // older than every edge of the batch, and its entries skip the age test.
-template <bool WORK>
+template <bool WORK, int MODE>
 __device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int cls, uint32_t grab,
                                                         unsigned long long* s_proc, CandQueue& cq, MatchQueue& mq,
                                                         Work& wk, uint32_t t0) {
@@ -1003,21 +992,24 @@ __device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int 
             const uint4* list = reinterpret_cast<const uint4*>(d.pool + 4ull * x.off_s + (1ull << lgs));
             const uint32_t last_pair = (n_s - 1u) >> 1;
             const uint32_t item = first + (uint32_t)i;
-            // one pass: kScanLoads 16-byte loads per lane (2 kScanLoads entries), all issued first;
-            // FULL: the pass lies inside the list, so no entry needs its position checked
-            // the tests of one pass on loaded entries q; FULL: inside the list (no position test);
-            // OLD: every entry older than the batch (no age test)
-            auto test = [&](const uint4 (&q)[kScanLoads], uint32_t j0, auto full, auto old) {
+            // kColWords: the entries' colour words, two per 8-byte load beside each entry pair
+            const uint2* words = reinterpret_cast<const uint2*>(list_words(d.pool, x.off_s, lgs));
+            // the tests of one pass on loaded entries q (and words cw); FULL: inside the list (no
+            // position test); OLD: every entry older than the batch (no age test)
+            auto test = [&](const uint4 (&q)[kScanLoads], const uint2 (&cw)[kScanLoads], uint32_t j0, auto full,
+                            auto old) {
                 constexpr bool FULL = decltype(full)::value, OLD = decltype(old)::value;
 #pragma unroll
                 for (uint32_t h = 0; h < kScanLoads; ++h) {
                     if (!FULL && j0 + 64u * h >= n_s) break;  // an empty part: uniform skip
                     const uint32_t jj = j0 + 64u * h + 2u * lane;
-                    const uint32_t w1 = q[h].x & kIdMask, w2 = q[h].z & kIdMask;
-                    const bool a1 =
-                        (FULL || jj < n_s) & (OLD || q[h].y < t) & colour_may_match(d, l, w1, q[h].x >> kIdBits);
-                    const bool a2 =
-                        (FULL || jj + 1u < n_s) & (OLD || q[h].w < t) & colour_may_match(d, l, w2, q[h].z >> kIdBits);
+                    const bool words_mode = MODE == (int)kColWords;
+                    const uint32_t w1 = words_mode ? q[h].x : q[h].x & kIdMask;
+                    const uint32_t w2 = words_mode ? q[h].z : q[h].z & kIdMask;
+                    const bool c1 = words_mode ? words_may_match(d, l, w1, cw[h].x) : colour_may_match(d, l, w1, q[h].x >> kIdBits);
+                    const bool c2 = words_mode ? words_may_match(d, l, w2, cw[h].y) : colour_may_match(d, l, w2, q[h].z >> kIdBits);
+                    const bool a1 = (FULL || jj < n_s) & (OLD || q[h].y < t) & c1;
+                    const bool a2 = (FULL || jj + 1u < n_s) & (OLD || q[h].w < t) & c2;
                     const unsigned m1 = __ballot_sync(0xFFFFFFFFu, a1), m2 = __ballot_sync(0xFFFFFFFFu, a2);
                     if (m1 | m2) {  // rare (about 1/m of the entries pass): uniform
                         if (a1) {
@@ -1034,20 +1026,24 @@ __device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int 
                         cq.n += __popc(m2);
                     }
                 }
-                if (cq.n >= 64u) cand_flush<WORK>(d, cq, false, s_proc, mq, wk);
+                if (cq.n >= 64u) cand_flush<WORK, MODE>(d, cq, false, s_proc, mq, wk);
             };
             auto pass = [&](uint32_t j0, auto full) {
                 constexpr bool FULL = decltype(full)::value;
                 uint4 q[kScanLoads];
+                uint2 cw[kScanLoads];
 #pragma unroll
                 for (uint32_t h = 0; h < kScanLoads; ++h) {
                     const uint32_t pr = (j0 >> 1) + 32u * h + lane;
-                    q[h] = list[FULL || pr < last_pair ? pr : last_pair];
+                    const uint32_t at = FULL || pr < last_pair ? pr : last_pair;
+                    q[h] = list[at];
+                    cw[h] = make_uint2(0u, 0u);
+                    if (MODE == (int)kColWords) cw[h] = words[at];
                 }
                 if (FULL && __shfl_sync(0xFFFFFFFFu, q[kScanLoads - 1].w, 31) < t0)
-                    test(q, j0, full, std::true_type{});
+                    test(q, cw, j0, full, std::true_type{});
                 else
-                    test(q, j0, full, std::false_type{});
+                    test(q, cw, j0, full, std::false_type{});
             };
             uint32_t j0 = 0;
             if (kScanFull)
@@ -1057,7 +1053,7 @@ __device__ __forceinline__ void drain_warp_bin_coloured(const StreamDev& d, int 
     }
 }
 
-template <int TILE, bool WORK, bool DIFF>
+template <int TILE, bool WORK, int MODE>
 __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, int cls, unsigned long long* s_proc,
                                                MatchQueue& mq, Work& wk) {
     constexpr uint32_t kPerWarp = 32 / TILE, kRounds = 4, kGrab = kPerWarp * kRounds;
@@ -1075,7 +1071,7 @@ __device__ __forceinline__ void drain_tile_bin(const StreamDev& d, int cls, unsi
             const bool valid = i < count;
             WorkItem x{};
             if (valid) x = items[i];
-            intersect_tile<TILE, WORK, DIFF>(d, x, valid, s_proc, mq, wk);
+            intersect_tile<TILE, WORK, MODE>(d, x, valid, s_proc, mq, wk);
         }
     }
 }
@@ -1097,7 +1093,7 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint
         for (unsigned long long i = i0; i < i1; ++i) {
             const WorkItem x = items[i];
             intersect_warp<WORK, MODE>(d, x, queue, wk, [&](bool has, uint32_t w) {
-                mq_push<WORK, MODE == (int)kColNone>(d, mq, has, x.s, x.l, w, s_proc, wk);
+                mq_push<WORK, MODE>(d, mq, has, x.s, x.l, w, s_proc, wk);
             });
         }
     }
@@ -1109,7 +1105,8 @@ __device__ __forceinline__ void drain_warp_bin(const StreamDev& d, int cls, uint
 template <bool WORK, int MODE>
 __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const BatchDev& b) {
     extern __shared__ unsigned long long s_proc[];
-    constexpr bool CAND = MODE == (int)kColInEntry;  // the scan-first warp path (candidate queue)
+    // the scan-first warp path (candidate queue): streams that store colours
+    constexpr bool CAND = MODE == (int)kColInEntry || MODE == (int)kColWords;
     __shared__ uint32_t s_queue[CAND ? 1 : 256 / 32][kQueue];  // intersect_warp's key queue
     __shared__ uint32_t s_cand[CAND ? 256 / 32 : 1][2][kCandQ];
     __shared__ uint32_t s_match[256 / 32][3][kMatchQ];
@@ -1140,10 +1137,10 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
             }
         };
         if constexpr (CAND) {
-            drain_warp_bin_coloured<WORK>(d, 5, kGrabHub, s_proc, cq, mq, wk, (uint32_t)b.t0);
+            drain_warp_bin_coloured<WORK, MODE>(d, 5, kGrabHub, s_proc, cq, mq, wk, (uint32_t)b.t0);
             mark(5);
-            drain_warp_bin_coloured<WORK>(d, 4, kGrabMid, s_proc, cq, mq, wk, (uint32_t)b.t0);
-            if (cq.n) cand_flush<WORK>(d, cq, true, s_proc, mq, wk);
+            drain_warp_bin_coloured<WORK, MODE>(d, 4, kGrabMid, s_proc, cq, mq, wk, (uint32_t)b.t0);
+            if (cq.n) cand_flush<WORK, MODE>(d, cq, true, s_proc, mq, wk);
             mark(4);
         } else {
             drain_warp_bin<WORK, MODE>(d, 5, kGrabHub, s_proc, queue, mq, wk);
@@ -1151,15 +1148,15 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
             drain_warp_bin<WORK, MODE>(d, 4, kGrabMid, s_proc, queue, mq, wk);
             mark(4);
         }
-        drain_tile_bin<32, WORK, MODE == (int)kColNone>(d, 3, s_proc, mq, wk);
+        drain_tile_bin<32, WORK, MODE>(d, 3, s_proc, mq, wk);
         mark(3);
-        drain_tile_bin<16, WORK, MODE == (int)kColNone>(d, 2, s_proc, mq, wk);
+        drain_tile_bin<16, WORK, MODE>(d, 2, s_proc, mq, wk);
         mark(2);
-        drain_tile_bin<8, WORK, MODE == (int)kColNone>(d, 1, s_proc, mq, wk);
+        drain_tile_bin<8, WORK, MODE>(d, 1, s_proc, mq, wk);
         mark(1);
-        drain_tile_bin<4, WORK, MODE == (int)kColNone>(d, 0, s_proc, mq, wk);
+        drain_tile_bin<4, WORK, MODE>(d, 0, s_proc, mq, wk);
         mark(0);
-        if (mq.n) mq_flush<WORK, MODE == (int)kColNone>(d, mq, mq.n, s_proc, wk);
+        if (mq.n) mq_flush<WORK, MODE>(d, mq, mq.n, s_proc, wk);
         if (WORK && blockIdx.x == 0 && threadIdx.x < kBins)
             d.ctrl->class_items[threadIdx.x] += d.ctrl->bin_count[threadIdx.x];
     }
@@ -1844,8 +1841,9 @@ __global__ void __launch_bounds__(256, REPT_COLOURED_BLOCKS) k_intersect(StreamD
     k_intersect_body<WORK, (int)kColInEntry>(d, b);
 }
 
-// Streams whose entries have colour words (several hash groups): hashes per entry, and probes for
-// about groups/m of the entries.
+// Streams whose entries have colour words (one hash group whose colour does not fit the entry: m > 256
+// or more than 2^24 nodes): the scan-first path with one hash per entry, and probes for about 1/m of
+// the entries.
 template <bool WORK>
 __global__ void __launch_bounds__(256, REPT_WORDS_BLOCKS) k_intersect_words(StreamDev d, BatchDev b) {
     k_intersect_body<WORK, (int)kColWords>(d, b);
