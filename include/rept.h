@@ -141,11 +141,12 @@ typedef struct rept_state rept_state;
  * n_nodes == 0; REPT_E_NOMEM / REPT_E_CUDA on allocation failure.  For c > m
  * with c mod m != 0 the handle also keeps Algorithm 2's triangle-pair
  * counters (16 + 12 * ceil(c/m) bytes per stream edge).
- * Speed: with one hash group (c <= m, or MASCOT with c == 1), 2 <= m <= 256
- * and n_nodes <= 2^24, each stored entry keeps its colour, and the
+ * Speed: with one hash group (c <= m, or MASCOT with c == 1) and m >= 2, each
+ * stored entry keeps its colour (in the entry's top 8 bits when m <= 256 and
+ * n_nodes <= 2^24, else in a word beside it, 25 % more pool), and the
  * intersection tests colours before it looks an edge up, so only about 1/m
- * of the lookups happen; other configurations look up every candidate wedge
- * edge (same counts, slower intersection).
+ * of the lookups happen; configurations with several hash groups look up
+ * every candidate wedge edge (same counts, slower intersection).
  */
 int rept_create(const rept_config* cfg, void* stream, rept_state** out);
 
