@@ -755,6 +755,16 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
 #endif
 constexpr uint32_t kGrabMid = REPT_GRAB_MID;  // class 4 items (33..256 entries) claimed per atomic
 constexpr uint32_t kGrabHub = REPT_GRAB_HUB;  // class 5 items (more entries) claimed per atomic
+// The scan-first path's claims: its items cost less each (about 1/m of the entries are probed), so
+// a warp takes more of them per atomic on the class cursor.
+#ifndef REPT_SCAN_GRAB_MID
+#define REPT_SCAN_GRAB_MID 8
+#endif
+#ifndef REPT_SCAN_GRAB_HUB
+#define REPT_SCAN_GRAB_HUB 2
+#endif
+constexpr uint32_t kScanGrabMid = REPT_SCAN_GRAB_MID;
+constexpr uint32_t kScanGrabHub = REPT_SCAN_GRAB_HUB;
 constexpr int kQueue = 192;  // one partial round (< 64 keys) + 128 new keys
 
 #ifndef REPT_PROBES_PER_LANE
@@ -1137,9 +1147,9 @@ __device__ __forceinline__ void k_intersect_body(const StreamDev& d, const Batch
             }
         };
         if constexpr (CAND) {
-            drain_warp_bin_coloured<WORK, MODE>(d, 5, kGrabHub, s_proc, cq, mq, wk, (uint32_t)b.t0);
+            drain_warp_bin_coloured<WORK, MODE>(d, 5, kScanGrabHub, s_proc, cq, mq, wk, (uint32_t)b.t0);
             mark(5);
-            drain_warp_bin_coloured<WORK, MODE>(d, 4, kGrabMid, s_proc, cq, mq, wk, (uint32_t)b.t0);
+            drain_warp_bin_coloured<WORK, MODE>(d, 4, kScanGrabMid, s_proc, cq, mq, wk, (uint32_t)b.t0);
             if (cq.n) cand_flush<WORK, MODE>(d, cq, true, s_proc, mq, wk);
             mark(4);
         } else {
@@ -1681,7 +1691,9 @@ __global__ void __launch_bounds__(1024, 2) k_rehash_huge_multi(const StreamDev* 
     k_rehash_huge_body(sd, launch_grid(), smem);
 }
 
-__global__ void k_insert(StreamDev d, BatchDev b) { k_insert_body(d, b, launch_grid()); }
+// 5 blocks of 256 threads per SM (48 registers): 2.79 against 2.93 ms per headline step at 56
+// registers and 4 blocks; at 6 blocks (40 registers) it spills.
+__global__ void __launch_bounds__(256, 5) k_insert(StreamDev d, BatchDev b) { k_insert_body(d, b, launch_grid()); }
 
 __global__ void k_insert_multi(const StreamDev* __restrict__ ds, const BatchDev* __restrict__ bs) {
     __shared__ StreamDev sd;
