@@ -7,10 +7,16 @@
 //   k_commit    move re-allocated tables (rehash), publish the new counts
 //   k_insert    insert each kept edge (nbr, stream index) into both
 //               endpoints' tables                              (Alg. 1 E^(i) <- E^(i) + {(u,v)})
-//   k_intersect for every edge t = (u, v): walk the smaller endpoint's table,
-//               probe the larger endpoint's table, and count the wedges whose
-//               two edges both arrived before t and carry the same kept
-//               colour; tally tau^(i), tau_u, tau_v, tau_w      (Alg. 1 UpdateTriangleCNT)
+//   k_sort_scan, k_sort_scatter
+//               order the edges that can close wedges into work classes by
+//               their smaller endpoint's entry count, grouped by the larger
+//               endpoint
+//   k_intersect for every edge t = (u, v): walk the smaller endpoint's list,
+//               look up the larger endpoint's table (for streams that store
+//               colours, only for entries whose colours may agree), and count
+//               the wedges whose two edges both arrived before t and carry
+//               the same kept colour; tally tau^(i), tau_u, tau_v, tau_w
+//                                                               (Alg. 1 UpdateTriangleCNT)
 // Counting after inserting is exact because every entry carries its stream
 // index and k_intersect only accepts entries with index < t: the state seen by
 // edge t is exactly the sequential algorithm's state before t.
@@ -742,11 +748,11 @@ __device__ __forceinline__ void intersect_tile(const StreamDev& d, const WorkIte
     mq_push<WORK, MODE>(d, mq, has, x.s, x.l, w, s_proc, wk);
 }
 
-// Edges whose smaller endpoint has more entries: a warp per edge.  Each pass reads 128 entries of
-// the smaller endpoint's list (two 16-byte loads per lane) and packs those older than the edge (and,
-// with stored colours, coloured alike for a kept processor) into the warp's shared-memory key queue.
-// The queue is probed with all 32 lanes, kProbesPerLane keys per lane, whenever it holds a full
-// round; a partial round waits for the next pass, so sparse candidates share round trips.
+// Edges whose smaller endpoint has more entries, streams without stored colours: a warp per edge.
+// Each pass reads 128 entries of the smaller endpoint's list (two 16-byte loads per lane) and packs
+// those older than the edge into the warp's shared-memory key queue.  The queue is probed with all 32
+// lanes, kProbesPerLane keys per lane, whenever it holds a full round; a partial round waits for the
+// next pass, so sparse candidates share round trips.
 #ifndef REPT_GRAB_MID
 #define REPT_GRAB_MID 4
 #endif
@@ -875,12 +881,12 @@ __device__ __forceinline__ void intersect_warp(const StreamDev& d, const WorkIte
     }
 }
 
-// Coloured streams (kColInEntry), warp classes: scan first, probe later.  A warp reads an item's
-// smaller-endpoint list 128 entries per pass (two 16-byte loads per lane, two entries each) and tests
-// every entry's colour against the larger endpoint by hash alone.  The few entries that pass (about
-// 1/m) join the warp's candidate queue together with the index of their work item; the queue is
-// probed 64 candidates at a time, whatever items they come from, so that an item with a handful of
-// candidates does not pay for a probe round of its own.
+// Streams that store colours (kColInEntry, kColWords), warp classes: scan first, probe later.  A warp
+// reads an item's smaller-endpoint list kScanPass entries per pass (kScanLoads 16-byte loads per
+// lane, two entries each) and tests every entry's colour against the larger endpoint by hash alone.
+// The few entries that pass (about 1/m) join the warp's candidate queue together with the index of
+// their work item; the queue is probed 64 candidates at a time, whatever items they come from, so
+// that an item with a handful of candidates does not pay for a probe round of its own.
 #ifndef REPT_SCAN_LOADS
 #define REPT_SCAN_LOADS 4
 #endif
